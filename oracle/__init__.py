@@ -1,0 +1,340 @@
+"""ORACLE -- test infrastructure only.
+
+A plain, slow CPU FP64 statement of what the DMRG sigma step computes.  Only
+tests/, __graft_entry__.smoke() and the cpu_baseline / reference leg of bench.py
+may import this package; the product path (paper_2501_18263_gb300) never does,
+and this package never imports the product path.
+
+Contents
+  * fci_sigma / fci_lowest / fci_rdm12: determinant-basis full CI (Eq. fulltensor,
+    Eq. 1 in the chemist convention), C kernel in fci.c.
+  * fock_hamiltonian: an independent Jordan-Wigner / Kronecker-product
+    construction of H on the whole Fock space (a pin for fci.c at L <= 4).
+  * projected_sigma: sigma = P H P psi for the two-site wave function of
+    Eq. Hamilton_act_nonsym, with P the MPS basis of Eq. DefinitionMPS written out
+    as explicit Fock-space vectors (exact for L <= 12).
+  * layout: the oracle's own reading of the block-sparse psi layout (integer
+    tables compared bit-exactly with the CUDA path's).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIBPATH = os.path.join(_LIBDIR, "liboracle_fci.so")
+_lock = threading.Lock()
+_lib = None
+
+LOCAL_Q = ((0, 0), (0, 1), (1, 0), (1, 1))
+
+
+def build(force: bool = False) -> str:
+    """Compile fci.c with gcc (OpenMP) into oracle/_lib/liboracle_fci.so."""
+    src = os.path.join(_HERE, "fci.c")
+    if (not force and os.path.exists(_LIBPATH)
+            and os.path.getmtime(_LIBPATH) >= os.path.getmtime(src)):
+        return _LIBPATH
+    os.makedirs(_LIBDIR, exist_ok=True)
+    tmp = _LIBPATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, src])
+    os.replace(tmp, _LIBPATH)
+    return _LIBPATH
+
+
+def _get():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.oracle_fci_sigma.argtypes = [ctypes.c_int] * 3 + [dp] * 4
+            lib.oracle_fci_sigma.restype = ctypes.c_int
+            lib.oracle_fci_rdm12.argtypes = [ctypes.c_int] * 3 + [dp] * 4
+            lib.oracle_fci_rdm12.restype = ctypes.c_int
+            lib.oracle_fci_strings.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32)]
+            lib.oracle_fci_strings.restype = ctypes.c_long
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ----------------------------------------------------------------------------
+# Full CI in the (n_alpha, n_beta) determinant space
+# ----------------------------------------------------------------------------
+
+def strings(L: int, n: int) -> np.ndarray:
+    """Occupation masks with n bits set among L, ascending (rank order)."""
+    from math import comb
+    out = np.zeros(comb(L, n), dtype=np.uint32)
+    got = _get().oracle_fci_strings(L, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    assert got == len(out)
+    return out
+
+
+def fci_dim(L, na, nb):
+    from math import comb
+    return comb(L, na) * comb(L, nb)
+
+
+def fci_sigma(t, v, na, nb, x):
+    """y = H x on the determinant space (rank order alpha-major)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    L = t.shape[0]
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    assert x.shape == (fci_dim(L, na, nb),)
+    y = np.empty_like(x)
+    rc = _get().oracle_fci_sigma(L, na, nb, _dp(t), _dp(v), _dp(x), _dp(y))
+    if rc:
+        raise ValueError("oracle_fci_sigma: bad arguments")
+    return y
+
+
+def fci_lowest(t, v, na, nb, k=1, tol=1e-12):
+    """Lowest k eigenpairs of H in the (na, nb) space (dense for small spaces, Lanczos otherwise)."""
+    L = t.shape[0]
+    n = fci_dim(L, na, nb)
+    if n <= 2500:
+        H = np.empty((n, n))
+        e = np.zeros(n)
+        for i in range(n):
+            e[i] = 1.0
+            H[:, i] = fci_sigma(t, v, na, nb, e)
+            e[i] = 0.0
+        w, U = np.linalg.eigh(0.5 * (H + H.T))
+        return w[:k], U[:, :k]
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    op = LinearOperator((n, n), matvec=lambda x: fci_sigma(t, v, na, nb, np.asarray(x).ravel()), dtype=np.float64)
+    rng = np.random.default_rng(0)
+    w, U = eigsh(op, k=k, which="SA", tol=tol, v0=rng.standard_normal(n), ncv=max(2 * k + 10, 24))
+    order = np.argsort(w)
+    return w[order], U[:, order]
+
+
+def fci_rdm12(na, nb, x, y, L):
+    """g1_ij = <x|E_ij|y>, g2_ijkl = <x| sum_st a+_is a+_kt a_lt a_js |y>."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    g1 = np.zeros((L, L))
+    g2 = np.zeros((L, L, L, L))
+    rc = _get().oracle_fci_rdm12(L, na, nb, _dp(x), _dp(y), _dp(g1), _dp(g2))
+    if rc:
+        raise ValueError("oracle_fci_rdm12: bad arguments")
+    return g1, g2
+
+
+def config_index(L, na, nb):
+    """Index of every determinant (rank order) in the local-state tensor of all L sites.
+
+    Site i carries local state s_i = 2 * alpha_i + beta_i; the tensor index is
+    sum_i s_i 4^(L-1-i) (site 0 most significant).
+    """
+    A = strings(L, na).astype(np.int64)
+    B = strings(L, nb).astype(np.int64)
+    ca = np.zeros(len(A), dtype=np.int64)
+    cb = np.zeros(len(B), dtype=np.int64)
+    for i in range(L):
+        w = 4 ** (L - 1 - i)
+        ca += ((A >> i) & 1) * 2 * w
+        cb += ((B >> i) & 1) * w
+    return (ca[:, None] + cb[None, :]).ravel()
+
+
+# ----------------------------------------------------------------------------
+# Independent Fock-space construction (Jordan-Wigner with Kronecker products)
+# ----------------------------------------------------------------------------
+
+def fock_creators(L):
+    """a+_{i,s} on the 4^L Fock space; local basis (0, beta, alpha, alpha beta)."""
+    import scipy.sparse as sp
+    ca = np.zeros((4, 4)); ca[2, 0] = 1.0; ca[3, 1] = 1.0      # a+_alpha
+    cb = np.zeros((4, 4)); cb[1, 0] = 1.0; cb[3, 2] = -1.0     # a+_beta
+    Z = np.diag([1.0, -1.0, -1.0, 1.0])
+    I = np.eye(4)
+    out = {}
+    for i in range(L):
+        for s, c in ((0, ca), (1, cb)):
+            m = sp.identity(1, format="csr")
+            for j in range(L):
+                f = Z if j < i else (c if j == i else I)
+                m = sp.kron(m, sp.csr_matrix(f), format="csr")
+            out[(i, s)] = m
+    return out
+
+
+def fock_hamiltonian(t, v):
+    """Dense-free sparse H on the whole Fock space, built term by term from a+ and a."""
+    import scipy.sparse as sp
+    L = t.shape[0]
+    cr = fock_creators(L)
+    an = {k: m.T.tocsr() for k, m in cr.items()}
+    H = sp.csr_matrix((4 ** L, 4 ** L))
+    for s in range(2):
+        for i in range(L):
+            for j in range(L):
+                if t[i, j] != 0.0:
+                    H = H + t[i, j] * (cr[(i, s)] @ an[(j, s)])
+    for s in range(2):
+        for tt in range(2):
+            for i in range(L):
+                for j in range(L):
+                    for k in range(L):
+                        for l in range(L):
+                            g = v[i, j, k, l]
+                            if g != 0.0:
+                                H = H + 0.5 * g * (cr[(i, s)] @ cr[(k, tt)] @ an[(l, tt)] @ an[(j, s)])
+    return H.tocsr()
+
+
+# ----------------------------------------------------------------------------
+# Block-sparse layout and the MPS basis as explicit Fock-space vectors
+# ----------------------------------------------------------------------------
+
+def _sectors(tab):
+    """tab: sequence of (na, nb, dim) -> (list of (na, nb), dims, offsets)."""
+    q = [(int(a), int(b)) for (a, b, _) in tab]
+    d = [int(x) for (_, _, x) in tab]
+    off = list(np.cumsum([0] + d[:-1]))
+    return q, d, off
+
+
+def enlarged(tab):
+    """Coarse sectors of block (x) site: sorted Q -> list of (s, block sector index, dim, row offset)."""
+    q, d, _ = _sectors(tab)
+    idx = {qq: k for k, qq in enumerate(q)}
+    Qs = sorted({(a + qs[0], b + qs[1]) for (a, b) in q for qs in LOCAL_Q})
+    out = {}
+    for Q in Qs:
+        subs, r = [], 0
+        for s, qs in enumerate(LOCAL_Q):
+            qa = (Q[0] - qs[0], Q[1] - qs[1])
+            if qa in idx:
+                subs.append((s, idx[qa], d[idx[qa]], r))
+                r += d[idx[qa]]
+        out[Q] = subs
+    return out
+
+
+def psi_layout(left_tab, right_tab, na, nb):
+    """int64 table (n_blocks, 7): QL_a, QL_b, QR_a, QR_b, rows, cols, element offset."""
+    el = enlarged(left_tab)
+    er = enlarged(right_tab)
+    rows, off = [], 0
+    for QL, subs in el.items():
+        QR = (na - QL[0], nb - QL[1])
+        if QR not in er:
+            continue
+        r = sum(x[2] for x in subs)
+        c = sum(x[2] for x in er[QR])
+        rows.append((QL[0], QL[1], QR[0], QR[1], r, c, off))
+        off += r * c
+    return np.array(rows, dtype=np.int64).reshape(-1, 7)
+
+
+def left_basis(left_bonds, left_sites):
+    """U[c, alpha]: block states of B_b as vectors over the configurations of sites 0..b-1."""
+    U = np.ones((1, 1))
+    for i, iso in enumerate(left_sites):
+        tab_prev = left_bonds[i].as_array() if hasattr(left_bonds[i], "as_array") else left_bonds[i]
+        tab_new = left_bonds[i + 1].as_array() if hasattr(left_bonds[i + 1], "as_array") else left_bonds[i + 1]
+        _, dp, op = _sectors(tab_prev)
+        qn, dn, on = _sectors(tab_new)
+        el = enlarged(tab_prev)
+        Un = np.zeros((U.shape[0], 4, sum(dn)))
+        for k, Q in enumerate(qn):
+            W = iso[Q]
+            for (s, kp, dim, r) in el[Q]:
+                Un[:, s, on[k]:on[k] + dn[k]] += U[:, op[kp]:op[kp] + dim] @ W[r:r + dim, :]
+        U = Un.reshape(U.shape[0] * 4, sum(dn))
+    return U
+
+
+def right_basis(L, bond, right_bonds, right_sites):
+    """V[c, beta]: block states of C_{bond+2} over the configurations of sites bond+2..L-1."""
+    V = np.ones((1, 1))
+    for m in range(L - 1, bond + 1, -1):
+        tab_prev = right_bonds[m + 1].as_array() if hasattr(right_bonds[m + 1], "as_array") else right_bonds[m + 1]
+        tab_new = right_bonds[m].as_array() if hasattr(right_bonds[m], "as_array") else right_bonds[m]
+        _, dp, op = _sectors(tab_prev)
+        qn, dn, on = _sectors(tab_new)
+        el = enlarged(tab_prev)
+        iso = right_sites[m]
+        Vn = np.zeros((4, V.shape[0], sum(dn)))
+        for k, Q in enumerate(qn):
+            W = iso[Q]
+            for (s, kp, dim, r) in el[Q]:
+                Vn[s, :, on[k]:on[k] + dn[k]] += V[:, op[kp]:op[kp] + dim] @ W[r:r + dim, :]
+        V = Vn.reshape(4 * V.shape[0], sum(dn))
+    return V
+
+
+def psi_to_dense(blocks, left_tab, right_tab, na, nb):
+    """Block list [(QL, QR, M)] -> Psi[alpha, s_b, s_b+1, beta] (zeros outside the sectors)."""
+    _, dl, ol = _sectors(left_tab)
+    _, dr, orr = _sectors(right_tab)
+    el = enlarged(left_tab)
+    er = enlarged(right_tab)
+    P = np.zeros((sum(dl), 4, 4, sum(dr)))
+    for (QL, QR, M) in blocks:
+        for (s, ka, da, ra) in el[tuple(QL)]:
+            for (s2, kc, dc, rc) in er[tuple(QR)]:
+                P[ol[ka]:ol[ka] + da, s, s2, orr[kc]:orr[kc] + dc] = M[ra:ra + da, rc:rc + dc]
+    return P
+
+
+def dense_to_psi(P, left_tab, right_tab, na, nb):
+    el = enlarged(left_tab)
+    er = enlarged(right_tab)
+    _, dl, ol = _sectors(left_tab)
+    _, dr, orr = _sectors(right_tab)
+    out = []
+    for QL, subs in el.items():
+        QR = (na - QL[0], nb - QL[1])
+        if QR not in er:
+            continue
+        rows = sum(x[2] for x in subs)
+        cols = sum(x[2] for x in er[QR])
+        M = np.zeros((rows, cols))
+        for (s, ka, da, ra) in subs:
+            for (s2, kc, dc, rc) in er[QR]:
+                M[ra:ra + da, rc:rc + dc] = P[ol[ka]:ol[ka] + da, s, s2, orr[kc]:orr[kc] + dc]
+        out.append((QL, QR, M))
+    return out
+
+
+def projected_sigma(t, v, na, nb, bp, psi_blocks, return_parts=False):
+    """sigma = P H P psi at the bond of `bp` (Eq. Hamilton_act_nonsym with the MPS basis as P).
+
+    psi is embedded in the full determinant space through the explicit basis
+    vectors of the left and right blocks, H is applied by fci_sigma, and the
+    result is projected back.  Exact (no truncation of H) for L <= 12.
+    """
+    L = bp.L
+    b = bp.bond
+    lt = bp.left_bonds[b].as_array()
+    rt = bp.right_bonds[b + 2].as_array()
+    U = left_basis(bp.left_bonds, bp.left_sites)
+    V = right_basis(L, b, bp.right_bonds, bp.right_sites)
+    P = psi_to_dense(psi_blocks, lt, rt, na, nb)
+    full = np.einsum("ca,astb,db->cstd", U, P, V, optimize=True).ravel()
+    cfg = config_index(L, na, nb)
+    x = full[cfg]
+    leak = float(np.dot(full, full) - np.dot(x, x))
+    y = fci_sigma(t, v, na, nb, x)
+    sfull = np.zeros(4 ** L)
+    sfull[cfg] = y
+    S = sfull.reshape(U.shape[0], 4, 4, V.shape[0])
+    Sd = np.einsum("ca,cstd,db->astb", U, S, V, optimize=True)
+    out = dense_to_psi(Sd, lt, rt, na, nb)
+    if return_parts:
+        return out, dict(U=U, V=V, leak=leak, x=x, y=y)
+    return out

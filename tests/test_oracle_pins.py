@@ -1,0 +1,210 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the mathematics.
+
+Each test would fail for a plausible mistake somewhere in oracle/fci.c or in the
+oracle's basis embedding (dropped term, wrong sign, transposed index, swapped
+spin, wrong 1/2), without re-typing the oracle's own formula.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2501_18263_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, val = line.split()
+                out[k] = float(val)
+    return out
+
+
+def test_spinless_torus_printed_energies():
+    """Sec. 3.1: exact E_GS = -7.2295..., E_1 = -7.2242... for the 4x4 torus, t = V = 1."""
+    g = _golden("spinless_torus_4x4.txt")
+    t, v, bonds = I.spinless_torus(4, 4, 1.0, 1.0)
+    assert len(bonds) == 32
+    w, _ = O.fci_lowest(t, v, 8, 0, k=2)
+    # printed to 4 decimals: agree to half a unit of the last printed digit
+    assert abs(w[0] - g["E_GS"]) <= 0.5e-4
+    assert abs(w[1] - g["E_1"]) <= 0.5e-4
+    assert w[0] < w[1]
+
+
+@pytest.mark.parametrize("L", [2, 3])
+def test_fci_sigma_equals_jordan_wigner_fock_matrix(L):
+    """fci.c (bit-string signs) against an independent Kronecker-product JW construction, every sector."""
+    t, v = I.synthetic_integrals(L, 7 + L)
+    H = O.fock_hamiltonian(t, v)
+    rng = np.random.default_rng(L)
+    for na in range(L + 1):
+        for nb in range(L + 1):
+            cfg = O.config_index(L, na, nb)
+            Hs = H[cfg][:, cfg].toarray()
+            x = rng.standard_normal(len(cfg))
+            np.testing.assert_allclose(O.fci_sigma(t, v, na, nb, x), Hs @ x, atol=1e-12, rtol=0)
+            # particle-number conservation of the reference matrix itself
+            other = np.setdiff1d(np.arange(4 ** L), cfg)
+            assert abs(H[other][:, cfg]).max() == 0.0 if len(other) else True
+
+
+def test_hubbard_dimer_closed_form():
+    """Two-site Hubbard, one alpha + one beta: E0 = U/2 - sqrt(U^2/4 + 4 t^2)."""
+    for hop, U in ((1.0, 4.0), (0.7, 0.3), (1.3, 10.0)):
+        t, v = I.hubbard_dimer(hop, U)
+        w, _ = O.fci_lowest(t, v, 1, 1)
+        assert w[0] == pytest.approx(U / 2 - math.sqrt(U * U / 4 + 4 * hop * hop), abs=1e-12)
+        # triplet (2 alpha): no double occupancy, no hopping possible -> E = 0
+        w2, _ = O.fci_lowest(t, v, 2, 0)
+        assert w2[0] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_noninteracting_closed_form():
+    """v = 0: E0 is the sum of the lowest na and nb one-electron levels of t."""
+    L = 6
+    t, _ = I.synthetic_integrals(L, 11)
+    v = np.zeros((L,) * 4)
+    eps = np.linalg.eigvalsh(t)
+    for na, nb in ((3, 3), (4, 2), (1, 0)):
+        w, _ = O.fci_lowest(t, v, na, nb)
+        assert w[0] == pytest.approx(eps[:na].sum() + eps[:nb].sum(), abs=1e-11)
+
+
+def test_diagonal_integrals_closed_form():
+    """Only (ii|jj) and t_ii: H is diagonal, E(det) = sum eps n + 1/2 sum_ij U_ij n_i n_j - 1/2 sum_i U_ii n_i."""
+    L = 4
+    rng = np.random.default_rng(3)
+    eps = rng.uniform(-1, 1, L)
+    Uij = rng.uniform(0, 1, (L, L))
+    Uij = Uij + Uij.T
+    t = np.diag(eps)
+    v = np.zeros((L,) * 4)
+    for i in range(L):
+        for j in range(L):
+            v[i, i, j, j] = Uij[i, j]
+    na, nb = 2, 1
+    A = O.strings(L, na)
+    B = O.strings(L, nb)
+    n = len(A) * len(B)
+    x = rng.standard_normal(n)
+    y = O.fci_sigma(t, v, na, nb, x)
+    k = 0
+    for a in A:
+        for b in B:
+            occ = np.array([((a >> i) & 1) + ((b >> i) & 1) for i in range(L)], dtype=float)
+            # a+_is a+_kt a_lt a_js with i=j, k=l: n_is n_kt - delta_{ik} delta_{st} n_is
+            e = eps @ occ + 0.5 * occ @ Uij @ occ - 0.5 * np.diag(Uij) @ occ
+            assert y[k] == pytest.approx(e * x[k], abs=1e-12)
+            k += 1
+
+
+def test_hermitian_and_spin_flip_symmetric():
+    L = 5
+    t, v = I.synthetic_integrals(L, 21)
+    rng = np.random.default_rng(0)
+    n = O.fci_dim(L, 3, 2)
+    x, y = rng.standard_normal(n), rng.standard_normal(n)
+    assert np.dot(x, O.fci_sigma(t, v, 3, 2, y)) == pytest.approx(np.dot(O.fci_sigma(t, v, 3, 2, x), y), rel=1e-13)
+    e32, _ = O.fci_lowest(t, v, 3, 2, k=3)
+    e23, _ = O.fci_lowest(t, v, 2, 3, k=3)
+    np.testing.assert_allclose(e32, e23, atol=1e-11)
+
+
+def test_orbital_rotation_invariance():
+    """Sec. 2.2: rotating t -> U t U^T and v -> U^(x4) v leaves the spectrum invariant."""
+    L = 5
+    t, v = I.synthetic_integrals(L, 5)
+    Q = I.random_orthogonal(L, 9)
+    tr = Q @ t @ Q.T
+    vr = np.einsum("ai,bj,ck,dl,ijkl->abcd", Q, Q, Q, Q, v, optimize=True)
+    e0, _ = O.fci_lowest(t, v, 2, 3, k=2)
+    e1, _ = O.fci_lowest(tr, vr, 2, 3, k=2)
+    np.testing.assert_allclose(e0, e1, atol=1e-11)
+    # a rotation by pi/2 of orbitals (0,1) is a swap of the two modes (Sec. 3.2, F2 remark)
+    S = np.eye(L)
+    S[[0, 1]] = S[[1, 0]]
+    e2, _ = O.fci_lowest(S @ t @ S.T, np.einsum("ai,bj,ck,dl,ijkl->abcd", S, S, S, S, v), 2, 3, k=2)
+    np.testing.assert_allclose(e0, e2, atol=1e-11)
+
+
+def test_rdm_contractions_and_energy():
+    L, na, nb = 5, 3, 2
+    t, v = I.synthetic_integrals(L, 8)
+    w, U = O.fci_lowest(t, v, na, nb)
+    psi = U[:, 0]
+    g1, g2 = O.fci_rdm12(na, nb, psi, psi, L)
+    assert np.trace(g1) == pytest.approx(na + nb, abs=1e-12)
+    np.testing.assert_allclose(np.einsum("ijkk->ij", g2), (na + nb - 1) * g1, atol=1e-12)
+    assert np.sum(t * g1) + 0.5 * np.sum(v * g2) == pytest.approx(w[0], abs=1e-11)
+    # Hellmann-Feynman at fixed psi is exact: dE/dt_ij = g1_ij
+    h = 1e-5
+    dt = np.zeros_like(t)
+    dt[1, 2] = dt[2, 1] = h
+    ep = psi @ O.fci_sigma(t + dt, v, na, nb, psi)
+    em = psi @ O.fci_sigma(t - dt, v, na, nb, psi)
+    assert (ep - em) / (2 * h) == pytest.approx(g1[1, 2] + g1[2, 1], abs=1e-8)
+
+
+def _full_bond(L, na, nb, bond, seed):
+    return I.bond_problem(L, na, nb, 4 ** L, bond, seed)
+
+
+def test_projected_sigma_matches_fock_space_projection():
+    """P H P psi through fci.c equals the projection through the JW Fock matrix (L = 4, truncated basis)."""
+    L, na, nb = 4, 2, 2
+    t, v = I.synthetic_integrals(L, 13)
+    bp = I.bond_problem(L, na, nb, 3, 1, seed=2)
+    sig, parts = O.projected_sigma(t, v, na, nb, bp, bp.psi, return_parts=True)
+    assert abs(parts["leak"]) < 1e-14
+    H = O.fock_hamiltonian(t, v)
+    lt, rt = bp.left_bonds[1].as_array(), bp.right_bonds[3].as_array()
+    U, V = parts["U"], parts["V"]
+    P = O.psi_to_dense(bp.psi, lt, rt, na, nb)
+    full = np.einsum("ca,astb,db->cstd", U, P, V).ravel()
+    S = (H @ full).reshape(U.shape[0], 4, 4, V.shape[0])
+    ref = np.einsum("ca,cstd,db->astb", U, S, V)
+    np.testing.assert_allclose(O.psi_to_dense(sig, lt, rt, na, nb), ref, atol=1e-13)
+
+
+def test_projected_hamiltonian_full_basis_and_variational_bound():
+    """Complete MPS basis: P H P has the FCI ground energy; truncated basis: energy above it (Sec. 2.1)."""
+    L, na, nb = 6, 3, 3
+    t, v = I.synthetic_integrals(L, 17)
+    efci, _ = O.fci_lowest(t, v, na, nb)
+    for D, exact in ((4 ** 3, True), (6, False)):
+        bp = I.bond_problem(L, na, nb, D, 2, seed=4)
+        lt, rt = bp.left_bonds[2].as_array(), bp.right_bonds[4].as_array()
+        shapes = [blk.shape for (_, _, blk) in bp.psi]
+        n = sum(r * c for (r, c) in shapes)
+        Hp = np.zeros((n, n))
+        for k in range(n):
+            e = np.zeros(n)
+            e[k] = 1.0
+            blocks, o = [], 0
+            for (QL, QR, blk) in bp.psi:
+                blocks.append((QL, QR, e[o:o + blk.size].reshape(blk.shape)))
+                o += blk.size
+            Hp[:, k] = np.concatenate([b.ravel() for (_, _, b) in O.projected_sigma(t, v, na, nb, bp, blocks)])
+        np.testing.assert_allclose(Hp, Hp.T, atol=1e-12)
+        e = np.linalg.eigvalsh(Hp)[0]
+        if exact:
+            assert e == pytest.approx(efci[0], abs=1e-10)
+        else:
+            assert e > efci[0] + 1e-6
+
+
+def test_psi_layout_is_sector_conserving():
+    bp = I.bond_problem(8, 4, 3, 20, 3, seed=1)
+    lt, rt = bp.left_bonds[3].as_array(), bp.right_bonds[5].as_array()
+    lay = O.psi_layout(lt, rt, 4, 3)
+    assert np.all(lay[:, 0] + lay[:, 2] == 4) and np.all(lay[:, 1] + lay[:, 3] == 3)
+    assert np.all(np.diff(lay[:, 6]) == (lay[:-1, 4] * lay[:-1, 5]))
+    assert [tuple(r[:2]) for r in lay] == sorted(tuple(r[:2]) for r in lay)
+    assert [blk.shape for (_, _, blk) in bp.psi] == [tuple(r[4:6]) for r in lay]
