@@ -1,0 +1,161 @@
+/*
+ * dmrg_gb300.h -- C ABI of the GB300 (sm_103a) two-site DMRG sigma engine.
+ *
+ * The library computes the Davidson sigma step sigma = H_eff psi of the
+ * two-site U(1)xU(1) ab-initio DMRG sweep (arXiv 2501.18263, Sec. 2.3,
+ * Eqs. Hamilton_act_nonsym and Hamilton_act_U1sym) for the Hamiltonian of
+ * Eq. 1 written in the chemist convention
+ *     H = sum_ij t_ij sum_s a+_is a_js
+ *       + 1/2 sum_ijkl (ij|kl) sum_st a+_is a+_kt a_lt a_js,
+ * i.e. the spin-independent case of Eq. 1 with v^{Eq.1}_ijkl = (ik|jl)/2.
+ * Everything numerical runs in the library's CUDA kernels on the stream given
+ * at creation; no entry point falls back to the CPU.
+ *
+ * Conventions shared by every entry point
+ *   - Orbital i of the chain carries local states (Sec. 2.1)
+ *       0 = empty, 1 = beta, 2 = alpha, 3 = alpha beta (= a+_alpha a+_beta |0>);
+ *     Jordan-Wigner order: chain position, then alpha before beta.
+ *   - A block basis is a list of (n_alpha, n_beta) sectors in ascending
+ *     lexicographic order, each with a dimension; states are numbered sector
+ *     by sector.  Sector tables are int32 triples (n_alpha, n_beta, dim).
+ *   - An enlarged block (left block x site, or site x right block) orders each
+ *     coarse sector Q by local state s = 0..3 ascending, each sub-block holding
+ *     the partner block's states of sector Q - q(s) in order.
+ *   - The two-site wave function at bond k (sites k, k+1 explicit) is stored as
+ *     dense row-major blocks (rows: coarse sector of L' = B_k x site k, cols:
+ *     coarse sector of R' = site k+1 x C_{k+2}); dmrg_layout gives the blocks.
+ *   - Device pointers are CUDA device addresses valid on the handle's device;
+ *     host pointers are ordinary CPU memory.  The caller owns every buffer it
+ *     passes; the library owns everything it allocates and frees it in
+ *     dmrg_destroy.
+ *
+ * Errors: every call returns a dmrg_status; nothing aborts or throws across
+ * the ABI.  dmrg_last_error() gives a message for the calling thread.  After
+ * DMRG_ERR_CUDA or DMRG_ERR_TIMEOUT the handle is in an undefined state and
+ * must be destroyed.
+ */
+#ifndef DMRG_GB300_H
+#define DMRG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmrg_handle dmrg_handle;
+
+typedef enum {
+  DMRG_OK = 0,
+  DMRG_ERR_ARG = 1,        /* invalid argument or call order */
+  DMRG_ERR_OOM = 2,        /* device allocation failed or over mem_cap_bytes */
+  DMRG_ERR_CUDA = 3,       /* CUDA runtime error (message in dmrg_last_error) */
+  DMRG_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up */
+  DMRG_ERR_NOCONV = 5,     /* Davidson reached max_iter without convergence */
+  DMRG_ERR_NONFINITE = 6,  /* NaN/Inf in inputs or results */
+  DMRG_ERR_STATE = 7       /* handle unusable */
+} dmrg_status;
+
+/* precision of the sigma GEMMs */
+enum {
+  DMRG_PREC_FP64 = 0,        /* FP64 operands, FP64 accumulation */
+  DMRG_PREC_MIXED_BF16 = 1   /* split BF16 operands on tcgen05, FP32 accumulation */
+};
+
+/*
+ * Problem statement (Sec. 2.1: d orbitals, N electrons, integrals t and v; the
+ * bond dimension D of Eq. DefinitionMPS).
+ *   t      host, L*L row-major, symmetric
+ *   v      host, L^4 row-major chemist (ij|kl), 8-fold symmetric
+ *   order  host permutation of 0..L-1 (chain position -> orbital) or NULL
+ *   D      maximal bond dimension for sweeps (dmrg_sweep may override)
+ *   seed   seed of the library's own initial state and start vectors
+ *   precision  DMRG_PREC_*
+ *   mem_cap_bytes  soft cap on the intermediate buffers of one sigma (0 = library default)
+ * The integrals are copied; the caller may free them after the call.
+ */
+typedef struct {
+  int32_t L, n_alpha, n_beta;
+  const double* t;
+  const double* v;
+  const int32_t* order;
+  int32_t D;
+  uint64_t seed;
+  int32_t precision;
+  uint64_t mem_cap_bytes;
+} dmrg_problem;
+
+/* Create a handle for one problem on the current CUDA device; `cuda_stream`
+ * is a cudaStream_t (NULL = default stream) on which all work is ordered. */
+dmrg_status dmrg_build_ops(const dmrg_problem* problem, void* cuda_stream, dmrg_handle** out);
+
+/*
+ * Load one site isometry of an MPS basis (Eq. DefinitionMPS in block-sparse
+ * form, Sec. 2.3).
+ *   side = 0: left-canonical site `site`, mapping B_site x site -> B_{site+1};
+ *             load in order site = 0, 1, ...
+ *   side = 1: right-canonical site `site`, mapping site x C_{site+1} -> C_site;
+ *             load in order site = L-1, L-2, ...
+ *   sectors   host int32[n_sectors*3] of the new block (n_alpha, n_beta, dim)
+ *   data      host doubles: for each new sector in order, the row-major
+ *             (rows x dim) isometry whose rows are the enlarged block's states
+ *             of that sector (ordering above) and whose columns are orthonormal.
+ */
+dmrg_status dmrg_load_site(dmrg_handle* h, int32_t site, int32_t side, int32_t n_sectors,
+                           const int32_t* sectors, const double* data);
+
+/* Build all renormalised block operators needed at `bond` (from the loaded
+ * isometries) and the bond's sigma plan. */
+dmrg_status dmrg_prepare(dmrg_handle* h, int32_t bond);
+
+/* Block table of the prepared bond: int64[n_blocks*7] rows
+ * (QL_alpha, QL_beta, QR_alpha, QR_beta, rows, cols, element offset); the
+ * pointer is library-owned and valid until the next call on the handle. */
+dmrg_status dmrg_layout(dmrg_handle* h, int32_t bond, int32_t* n_blocks, const int64_t** table,
+                        int64_t* psi_size);
+
+/* sigma = H_eff psi at `bond` (device buffers of psi_size doubles). */
+dmrg_status dmrg_sigma(dmrg_handle* h, int32_t bond, const double* psi_dev, double* sigma_dev);
+
+/* Same with host buffers: host->device copy of psi, sigma, device->host copy. */
+dmrg_status dmrg_sigma_host(dmrg_handle* h, int32_t bond, const double* psi_host, double* sigma_host);
+
+/* Lowest eigenpair of H_eff at `bond` by Davidson; psi_dev is the start vector
+ * on entry and the normalised eigenvector on exit; *energy its Rayleigh
+ * quotient (from an FP64 sigma).  tol bounds the residual 2-norm. */
+dmrg_status dmrg_davidson(dmrg_handle* h, int32_t bond, double* psi_dev, double tol, int32_t max_iter,
+                          double* energy, int32_t* iterations);
+
+/* n_sweeps full two-site sweeps (left-to-right then right-to-left) with bond
+ * dimension D_schedule[s] (host, or NULL for problem->D); energies[s] (host)
+ * receives the Davidson energy of the last step of sweep s.  Starts from the
+ * loaded right-canonical basis at bond 0 if one was loaded, otherwise from a
+ * seeded basis of kept product states. */
+dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,
+                       double* energies);
+
+/* Reduced density matrices at the prepared bond (Sec. 2.2 uses them for
+ * orbital rotations): with x = lam_dev, y = psi_dev (device, psi_size doubles)
+ *   g1[i*L+j]             += <x| sum_s a+_is a_js |y>
+ *   g2[((i*L+j)*L+k)*L+l] += <x| sum_st a+_is a+_kt a_lt a_js |y>
+ * so that dE/dt = g1 and dE/dv = g2/2 for x = y = the normalised eigenvector.
+ * g1, g2 are device buffers (L^2 and L^4 doubles). */
+dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi_dev, const double* lam_dev,
+                                double* g1_dev, double* g2_dev);
+
+/* Statistics of the prepared bond: int64[8] = psi_size, n_terms,
+ * flops_stage1, flops_stage2, operator_bytes, gemm_problems, gemm_segments,
+ * device kernel launches of one sigma. */
+dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out8);
+
+void dmrg_destroy(dmrg_handle* h);
+
+/* Thread-local message of the last failing call (empty string if none). */
+const char* dmrg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMRG_GB300_H */

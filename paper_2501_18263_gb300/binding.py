@@ -1,0 +1,183 @@
+"""Thin ctypes binding of the C ABI in include/dmrg_gb300.h (argument marshalling only).
+
+Device buffers are passed as integer CUDA addresses (for example
+torch.Tensor.data_ptr()); host buffers as numpy arrays.  Loading fails loudly
+when the compiled sm_103a library is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_LIB = os.path.join(_HERE, "_lib", "libdmrg_gb300.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOCONV, ERR_NONFINITE, ERR_STATE = range(8)
+PREC_FP64, PREC_MIXED_BF16 = 0, 1
+
+SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
+           "dmrg_sigma_host", "dmrg_davidson", "dmrg_sweep", "dmrg_sigma_backward", "dmrg_stats",
+           "dmrg_destroy", "dmrg_last_error"]
+
+
+class DmrgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"dmrg status {status}: {msg}")
+        self.status = status
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("n_alpha", ctypes.c_int32), ("n_beta", ctypes.c_int32),
+                ("t", ctypes.POINTER(ctypes.c_double)), ("v", ctypes.POINTER(ctypes.c_double)),
+                ("order", ctypes.POINTER(ctypes.c_int32)), ("D", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int32), ("mem_cap_bytes", ctypes.c_uint64)]
+
+
+_libs = {}
+
+
+def load_library(path: str | None = None):
+    path = path or DEFAULT_LIB
+    if path in _libs:
+        return _libs[path]
+    if not os.path.exists(path):
+        raise RuntimeError(f"compiled DMRG library not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+    i32, f64 = ctypes.c_int32, ctypes.c_double
+    sig = {
+        "dmrg_build_ops": ([ctypes.POINTER(_Problem), vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "dmrg_load_site": ([vp, i32, i32, i32, ip, dp], ctypes.c_int),
+        "dmrg_prepare": ([vp, i32], ctypes.c_int),
+        "dmrg_layout": ([vp, i32, ip, ctypes.POINTER(i64p), i64p], ctypes.c_int),
+        "dmrg_sigma": ([vp, i32, vp, vp], ctypes.c_int),
+        "dmrg_sigma_host": ([vp, i32, dp, dp], ctypes.c_int),
+        "dmrg_davidson": ([vp, i32, vp, f64, i32, dp, ip], ctypes.c_int),
+        "dmrg_sweep": ([vp, i32, ip, f64, dp], ctypes.c_int),
+        "dmrg_sigma_backward": ([vp, i32, vp, vp, vp, vp], ctypes.c_int),
+        "dmrg_stats": ([vp, i64p], ctypes.c_int),
+        "dmrg_destroy": ([vp], None),
+        "dmrg_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _libs[path] = lib
+    return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Dmrg:
+    """One problem (integrals, electron counts, D) bound to a CUDA stream."""
+
+    def __init__(self, t, v, na, nb, D=256, order=None, seed=0, precision=PREC_FP64, mem_cap=0,
+                 stream=0, lib=None):
+        self.lib = load_library(lib)
+        self.t = np.ascontiguousarray(t, dtype=np.float64)
+        self.v = np.ascontiguousarray(v, dtype=np.float64)
+        self.L = int(self.t.shape[0])
+        self.na, self.nb = int(na), int(nb)
+        self._order = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+        p = _Problem(self.L, self.na, self.nb, _dp(self.t), _dp(self.v),
+                     self._order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if self._order is not None else None,
+                     int(D), int(seed), int(precision), int(mem_cap))
+        h = ctypes.c_void_p()
+        self._check(self.lib.dmrg_build_ops(ctypes.byref(p), ctypes.c_void_p(int(stream)), ctypes.byref(h)))
+        self.h = h
+
+    def _check(self, st):
+        if st != OK:
+            raise DmrgError(st, self.lib.dmrg_last_error().decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dmrg_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    # -- basis
+    def load_site(self, site, side, sectors, mats):
+        sec = np.ascontiguousarray(np.asarray(sectors, dtype=np.int32).reshape(-1, 3))
+        data = np.ascontiguousarray(np.concatenate([np.asarray(m, dtype=np.float64).ravel() for m in mats]))
+        self._check(self.lib.dmrg_load_site(self.h, site, side, len(sec),
+                                            sec.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(data)))
+
+    def load_bond_problem(self, bp):
+        """Load the left-canonical and right-canonical isometries of an inputs.BondProblem."""
+        for i, iso in enumerate(bp.left_sites):
+            sec = bp.left_bonds[i + 1]
+            self.load_site(i, 0, sec.as_array(), [iso[q] for q in sec.q])
+        for m in range(bp.L - 1, bp.bond + 1, -1):
+            sec = bp.right_bonds[m]
+            self.load_site(m, 1, sec.as_array(), [bp.right_sites[m][q] for q in sec.q])
+
+    def prepare(self, bond):
+        self._check(self.lib.dmrg_prepare(self.h, bond))
+
+    def layout(self, bond):
+        n = ctypes.c_int32()
+        tab = ctypes.POINTER(ctypes.c_int64)()
+        size = ctypes.c_int64()
+        self._check(self.lib.dmrg_layout(self.h, bond, ctypes.byref(n), ctypes.byref(tab), ctypes.byref(size)))
+        arr = np.ctypeslib.as_array(tab, shape=(n.value * 7,)).reshape(-1, 7).copy() if n.value else np.zeros((0, 7), np.int64)
+        return arr, size.value
+
+    # -- compute
+    def sigma(self, bond, psi_ptr, sig_ptr):
+        self._check(self.lib.dmrg_sigma(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.c_void_p(int(sig_ptr))))
+
+    def sigma_host(self, bond, psi):
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        out = np.empty_like(psi)
+        self._check(self.lib.dmrg_sigma_host(self.h, bond, _dp(psi), _dp(out)))
+        return out
+
+    def davidson(self, bond, psi_ptr, tol=1e-8, max_iter=100, check=True):
+        e = ctypes.c_double()
+        it = ctypes.c_int32()
+        st = self.lib.dmrg_davidson(self.h, bond, ctypes.c_void_p(int(psi_ptr)), float(tol), int(max_iter),
+                                    ctypes.byref(e), ctypes.byref(it))
+        if check:
+            self._check(st)
+        return e.value, it.value
+
+    def sweep(self, n_sweeps, D_schedule=None, tol=1e-8):
+        e = np.zeros(n_sweeps)
+        Ds = None
+        if D_schedule is not None:
+            Ds = np.ascontiguousarray(D_schedule, dtype=np.int32)
+        self._check(self.lib.dmrg_sweep(self.h, n_sweeps,
+                                        Ds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if Ds is not None else None,
+                                        float(tol), _dp(e)))
+        return e
+
+    def sigma_backward(self, bond, psi_ptr, lam_ptr, g1_ptr, g2_ptr):
+        self._check(self.lib.dmrg_sigma_backward(self.h, bond, ctypes.c_void_p(int(psi_ptr)),
+                                                 ctypes.c_void_p(int(lam_ptr)), ctypes.c_void_p(int(g1_ptr)),
+                                                 ctypes.c_void_p(int(g2_ptr))))
+
+    def stats(self):
+        o = np.zeros(8, dtype=np.int64)
+        self._check(self.lib.dmrg_stats(self.h, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        keys = ["psi_size", "n_terms", "flops_stage1", "flops_stage2", "op_bytes", "gemm_problems",
+                "gemm_segments", "launches_per_sigma"]
+        return dict(zip(keys, (int(x) for x in o)))
+
+
+def pack_psi(blocks):
+    return np.concatenate([np.asarray(b, dtype=np.float64).ravel() for (_, _, b) in blocks])
+
+
+def unpack_psi(flat, layout):
+    out = []
+    for row in layout:
+        qa, qb, ra, rb, r, c, off = (int(x) for x in row)
+        out.append(((qa, qb), (ra, rb), np.asarray(flat[off:off + r * c]).reshape(r, c)))
+    return out

@@ -1,0 +1,305 @@
+// C ABI (include/dmrg_gb300.h) over the host core.  Every entry point catches
+// all exceptions and returns a status; messages are kept per thread.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <stdexcept>
+#include <string>
+
+#include "../../include/dmrg_gb300.h"
+#include "core/core.h"
+#include "exec_errors.h"
+
+struct dmrg_handle {
+  std::unique_ptr<dmrg::Exec> ex;
+  std::unique_ptr<dmrg::Engine> eng;
+  int L = 0;
+  int left_loaded = 0;     // number of left sites loaded
+  int right_loaded = -1;   // lowest right site loaded (L if none)
+  bool any_loaded = false;
+};
+
+namespace {
+thread_local std::string g_err;
+
+dmrg_status fail(dmrg_status s, const std::string& m) {
+  g_err = m;
+  return s;
+}
+
+template <class F>
+dmrg_status guard(F&& f) {
+  try {
+    g_err.clear();
+    return f();
+  } catch (const dmrg::CudaError& e) {
+    return fail(DMRG_ERR_CUDA, e.what());
+  } catch (const dmrg::OomError& e) {
+    return fail(DMRG_ERR_OOM, e.what());
+  } catch (const dmrg::TimeoutError& e) {
+    return fail(DMRG_ERR_TIMEOUT, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(DMRG_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(DMRG_ERR_ARG, e.what());
+  } catch (...) {
+    return fail(DMRG_ERR_STATE, "unknown error");
+  }
+}
+
+bool finite(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+dmrg_status ensure_bond(dmrg_handle* h, int bond) {
+  if (bond < 0 || bond > h->L - 2) return fail(DMRG_ERR_ARG, "bond out of range");
+  if (h->eng->bond() != bond) {
+    h->eng->build_left_blocks(bond);
+    h->eng->build_right_blocks(bond + 2);
+    h->eng->prepare_bond(bond);
+  }
+  return DMRG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+dmrg_status dmrg_build_ops(const dmrg_problem* p, void* stream, dmrg_handle** out) {
+  return guard([&]() -> dmrg_status {
+    if (!p || !out) return fail(DMRG_ERR_ARG, "null argument");
+    *out = nullptr;
+    const int L = p->L;
+    if (L < 2 || L > 64) return fail(DMRG_ERR_ARG, "L must be in [2, 64]");
+    if (p->n_alpha < 0 || p->n_beta < 0 || p->n_alpha > L || p->n_beta > L)
+      return fail(DMRG_ERR_ARG, "electron counts out of range");
+    if (!p->t || !p->v) return fail(DMRG_ERR_ARG, "t and v are required");
+    if (p->precision != DMRG_PREC_FP64 && p->precision != DMRG_PREC_MIXED_BF16)
+      return fail(DMRG_ERR_ARG, "unknown precision");
+    const size_t L2 = size_t(L) * L, L4 = L2 * L2;
+    if (!finite(p->t, L2) || !finite(p->v, L4)) return fail(DMRG_ERR_NONFINITE, "non-finite integrals");
+    std::vector<int> ord(L);
+    for (int i = 0; i < L; ++i) ord[i] = p->order ? p->order[i] : i;
+    {
+      std::vector<int> seen(L, 0);
+      for (int i = 0; i < L; ++i) {
+        if (ord[i] < 0 || ord[i] >= L || seen[ord[i]]) return fail(DMRG_ERR_ARG, "order is not a permutation");
+        seen[ord[i]] = 1;
+      }
+    }
+    dmrg::Problem P;
+    P.L = L;
+    P.na = p->n_alpha;
+    P.nb = p->n_beta;
+    P.D = p->D > 0 ? p->D : 256;
+    P.seed = p->seed;
+    P.precision = p->precision;
+    P.mem_cap = p->mem_cap_bytes;
+    P.t.resize(L2);
+    P.v.resize(L4);
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j < L; ++j) P.t[size_t(i) * L + j] = p->t[size_t(ord[i]) * L + ord[j]];
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j < L; ++j)
+        for (int k = 0; k < L; ++k)
+          for (int l = 0; l < L; ++l)
+            P.v[((size_t(i) * L + j) * L + k) * L + l] =
+                p->v[((size_t(ord[i]) * L + ord[j]) * L + ord[k]) * L + ord[l]];
+    auto h = std::make_unique<dmrg_handle>();
+    h->L = L;
+    h->right_loaded = L;
+    h->ex.reset(dmrg::make_cuda_exec(stream, p->precision));
+    h->eng = std::make_unique<dmrg::Engine>(P, h->ex.get());
+    *out = h.release();
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_load_site(dmrg_handle* h, int32_t site, int32_t side, int32_t n_sectors,
+                           const int32_t* sectors, const double* data) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !sectors || !data || n_sectors <= 0) return fail(DMRG_ERR_ARG, "null argument");
+    if (site < 0 || site >= h->L) return fail(DMRG_ERR_ARG, "site out of range");
+    dmrg::Sectors s;
+    for (int k = 0; k < n_sectors; ++k) {
+      s.q.push_back(dmrg::QN{sectors[3 * k], sectors[3 * k + 1]});
+      s.dim.push_back(sectors[3 * k + 2]);
+      if (sectors[3 * k + 2] <= 0) return fail(DMRG_ERR_ARG, "sector dimension must be positive");
+      if (k > 0 && !(s.q[k - 1] < s.q[k])) return fail(DMRG_ERR_ARG, "sectors must be strictly ascending");
+    }
+    if (side == 0) {
+      if (site != h->left_loaded) return fail(DMRG_ERR_ARG, "left sites must be loaded in order 0, 1, ...");
+    } else if (side == 1) {
+      if (site != h->right_loaded - 1) return fail(DMRG_ERR_ARG, "right sites must be loaded in order L-1, L-2, ...");
+    } else {
+      return fail(DMRG_ERR_ARG, "side must be 0 or 1");
+    }
+    // rows of each isometry come from the enlarged block; the engine validates them
+    dmrg::Enlarged E;
+    const dmrg::Block& prev = side == 0 ? h->eng->left_block(site) : h->eng->right_block(site + 1);
+    E.build(prev.sec, side == 0);
+    std::vector<const double*> mats;
+    size_t off = 0;
+    for (int k = 0; k < n_sectors; ++k) {
+      int c = E.coarse.find(s.q[k]);
+      if (c < 0) return fail(DMRG_ERR_ARG, "sector not reachable from the neighbouring block");
+      if (s.dim[k] > E.coarse.dim[c]) return fail(DMRG_ERR_ARG, "isometry wider than the enlarged sector");
+      mats.push_back(data + off);
+      size_t n = size_t(E.coarse.dim[c]) * s.dim[k];
+      if (!finite(data + off, n)) return fail(DMRG_ERR_NONFINITE, "non-finite isometry");
+      off += n;
+    }
+    if (side == 0) {
+      h->eng->load_left(site, s, mats);
+      h->left_loaded = site + 1;
+    } else {
+      h->eng->load_right(site, s, mats);
+      h->right_loaded = site;
+    }
+    h->any_loaded = true;
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_prepare(dmrg_handle* h, int32_t bond) {
+  return guard([&]() -> dmrg_status {
+    if (!h) return fail(DMRG_ERR_ARG, "null handle");
+    if (bond < 0 || bond > h->L - 2) return fail(DMRG_ERR_ARG, "bond out of range");
+    if (h->left_loaded < bond && !h->eng->left_block(bond).valid)
+      return fail(DMRG_ERR_ARG, "left sites 0..bond-1 are not loaded");
+    if (h->right_loaded > bond + 2 && !h->eng->right_block(bond + 2).valid)
+      return fail(DMRG_ERR_ARG, "right sites bond+2..L-1 are not loaded");
+    h->eng->build_left_blocks(bond);
+    h->eng->build_right_blocks(bond + 2);
+    h->eng->prepare_bond(bond);
+    h->eng->exec()->sync();
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_layout(dmrg_handle* h, int32_t bond, int32_t* n_blocks, const int64_t** table,
+                        int64_t* psi_size) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !n_blocks || !table) return fail(DMRG_ERR_ARG, "null argument");
+    if (h->eng->bond() != bond) return fail(DMRG_ERR_ARG, "bond not prepared (call dmrg_prepare)");
+    *n_blocks = int32_t(h->eng->layout().size() / 7);
+    *table = h->eng->layout().data();
+    if (psi_size) *psi_size = h->eng->psi_size();
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_sigma(dmrg_handle* h, int32_t bond, const double* psi, double* sig) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !psi || !sig) return fail(DMRG_ERR_ARG, "null argument");
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    h->eng->sigma_precision(psi, sig, h->eng->problem().precision);
+    h->eng->exec()->sync();
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_sigma_host(dmrg_handle* h, int32_t bond, const double* psi, double* sig) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !psi || !sig) return fail(DMRG_ERR_ARG, "null argument");
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    dmrg::Exec* ex = h->eng->exec();
+    const size_t bytes = size_t(h->eng->psi_size()) * sizeof(double);
+    double* d = static_cast<double*>(ex->alloc(2 * bytes));
+    ex->h2d(d, psi, bytes);
+    h->eng->sigma_precision(d, d + h->eng->psi_size(), h->eng->problem().precision);
+    ex->d2h(sig, d + h->eng->psi_size(), bytes);
+    ex->sync();
+    ex->release(d);
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_davidson(dmrg_handle* h, int32_t bond, double* psi, double tol, int32_t max_iter,
+                          double* energy, int32_t* iterations) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !psi) return fail(DMRG_ERR_ARG, "null argument");
+    if (!(tol > 0)) return fail(DMRG_ERR_ARG, "tol must be positive");
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    int it = 0;
+    double e = h->eng->davidson(psi, tol, max_iter > 0 ? max_iter : 100, 24, &it, 1);
+    h->eng->exec()->sync();
+    if (energy) *energy = e;
+    if (iterations) *iterations = it;
+    if (!std::isfinite(e)) return fail(DMRG_ERR_NONFINITE, "non-finite energy");
+    if (h->eng->last_rnorm > tol) return fail(DMRG_ERR_NOCONV, "Davidson did not reach the tolerance");
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,
+                       double* energies) {
+  return guard([&]() -> dmrg_status {
+    if (!h || n_sweeps <= 0) return fail(DMRG_ERR_ARG, "bad arguments");
+    if (h->L < 3) return fail(DMRG_ERR_ARG, "sweeps need L >= 3");
+    if (!(tol > 0)) return fail(DMRG_ERR_ARG, "tol must be positive");
+    std::vector<int> D(n_sweeps);
+    for (int s = 0; s < n_sweeps; ++s) {
+      D[s] = D_schedule ? D_schedule[s] : h->eng->problem().D;
+      if (D[s] <= 0) return fail(DMRG_ERR_ARG, "D must be positive");
+    }
+    if (h->right_loaded > 2 && h->any_loaded && !h->eng->right_block(2).valid)
+      return fail(DMRG_ERR_ARG, "a partially loaded basis must reach site 2 for sweeps");
+    h->eng->set_D(D[0]);
+    std::vector<double> e = h->eng->run_sweeps(n_sweeps, D.data(), tol);
+    h->eng->exec()->sync();
+    if (energies)
+      for (int s = 0; s < n_sweeps; ++s) energies[s] = e[s];
+    for (double x : e)
+      if (!std::isfinite(x)) return fail(DMRG_ERR_NONFINITE, "non-finite energy");
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi, const double* lam,
+                                double* g1, double* g2) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !psi || !lam || !g1 || !g2) return fail(DMRG_ERR_ARG, "null argument");
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    h->eng->rdm(lam, psi, g1, g2);
+    h->eng->exec()->sync();
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_stats(dmrg_handle* h, int64_t* o) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !o) return fail(DMRG_ERR_ARG, "null argument");
+    const dmrg::BondStats& s = h->eng->stats();
+    o[0] = s.psi_size;
+    o[1] = s.n_terms;
+    o[2] = s.flops_stage1;
+    o[3] = s.flops_stage2;
+    o[4] = s.op_bytes;
+    o[5] = s.n_gemm_problems;
+    o[6] = s.n_gemm_segments;
+    o[7] = s.launches_per_sigma;
+    return DMRG_OK;
+  });
+}
+
+void dmrg_destroy(dmrg_handle* h) {
+  try {
+    if (h) {
+      h->eng.reset();
+      h->ex.reset();
+      delete h;
+    }
+  } catch (...) {
+  }
+}
+
+const char* dmrg_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

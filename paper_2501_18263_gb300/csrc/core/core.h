@@ -1,0 +1,221 @@
+// Host core of the two-site U(1)xU(1) DMRG sigma engine (Sec. 2.3, Eqs.
+// Hamilton_act_nonsym / Hamilton_act_U1sym): sector tables, the catalogue of
+// normal and complementary block operators, the blocking / renormalisation /
+// sigma / wave-function-transformation plans, and the Davidson and sweep
+// drivers.  Everything numerical is delegated to an Exec (exec.h).
+#pragma once
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../exec.h"
+
+namespace dmrg {
+
+struct QN {
+  int a = 0, b = 0;  // n_alpha, n_beta
+  bool operator<(const QN& o) const { return a < o.a || (a == o.a && b < o.b); }
+  bool operator==(const QN& o) const { return a == o.a && b == o.b; }
+  bool operator!=(const QN& o) const { return !(*this == o); }
+  QN operator+(const QN& o) const { return {a + o.a, b + o.b}; }
+  QN operator-(const QN& o) const { return {a - o.a, b - o.b}; }
+  int n() const { return a + b; }
+};
+
+// local states of one orbital: 0 empty, 1 beta, 2 alpha, 3 alpha beta (= a+_a a+_b |0>)
+extern const QN kLocalQ[4];
+
+struct Sectors {
+  std::vector<QN> q;
+  std::vector<int> dim;
+  std::vector<int64_t> off;
+  int64_t total = 0;
+  void finalize();
+  int find(const QN& x) const;  // -1 if absent
+};
+
+// Enlarged block: left (block (x) site) or right (site (x) block).  Coarse
+// sectors Q hold fine sub-blocks for s = 0..3 ascending.
+struct Enlarged {
+  bool left = true;
+  Sectors coarse;
+  // fine sectors, ordered by (coarse, s)
+  std::vector<int> f_coarse, f_s, f_part, f_dim, f_row;
+  std::vector<std::vector<int>> coarse_fines;
+  std::vector<std::vector<int>> part_s_to_fine;  // [part][s] -> fine or -1
+  void build(const Sectors& part, bool is_left);
+  QN fq(int f) const { return coarse.q[f_coarse[f]]; }
+};
+
+enum OpType { OP_H = 0, OP_C, OP_A, OP_B, OP_S, OP_T, OP_P, OP_Q };
+
+struct OpKey {
+  int type, i, j;
+  bool operator<(const OpKey& o) const {
+    if (type != o.type) return type < o.type;
+    if (i != o.i) return i < o.i;
+    return j < o.j;
+  }
+};
+
+struct OpBlk {
+  int r, c;          // row / col sector (block sectors, or fine sectors on enlarged blocks)
+  int rows, cols;
+  int64_t off;       // element offset in the owning arena
+  int ident = 0;     // enlarged only: block is c * identity (never read as a matrix)
+};
+
+struct Op {
+  QN delta;
+  int odd = 0;
+  std::vector<OpBlk> blk;
+  std::map<int, int> by_col;   // col sector -> index in blk  (one block per column sector)
+  std::map<int, int> by_row;
+};
+
+struct OpSet {
+  std::map<OpKey, Op> ops;
+  double* arena = nullptr;
+  int64_t n_elem = 0;
+  const Op* get(int type, int i, int j = 0) const {
+    auto it = ops.find(OpKey{type, i, j});
+    return it == ops.end() ? nullptr : &it->second;
+  }
+};
+
+// 4x4 matrix on one orbital with definite fermion parity
+struct Site4 {
+  double m[4][4] = {};
+  int odd = 0;
+  bool zero() const;
+};
+
+struct Problem {
+  int L = 0, na = 0, nb = 0;
+  std::vector<double> t, v;  // permuted into chain order
+  int D = 0;
+  uint64_t seed = 0;
+  int precision = 0;
+  size_t mem_cap = 0;
+  double h(int p, int q) const;                 // spin-orbital one-body
+  double g(int p, int q, int r, int s) const;   // spin-orbital (pq|rs)
+};
+
+struct Block {
+  bool valid = false;
+  Sectors sec;
+  OpSet ops;
+};
+
+struct Iso {  // site isometry: enlarged coarse sector -> new block sector
+  bool valid = false;
+  Sectors out;                     // new block sectors
+  std::vector<double*> mat;        // per out sector: rows(enlarged Q) x out.dim, row-major
+  std::vector<int> rows;
+  double* arena = nullptr;
+};
+
+struct BondStats {
+  int64_t psi_size = 0;
+  int n_terms = 0;
+  int64_t flops_stage1 = 0, flops_stage2 = 0;
+  int64_t op_bytes = 0;   // algorithmic operator bytes read by one sigma (FP64)
+  int n_gemm_problems = 0, n_gemm_segments = 0;
+  int launches_per_sigma = 0;
+};
+
+class Engine {
+ public:
+  Engine(const Problem& p, Exec* ex);
+  ~Engine();
+
+  const Problem& problem() const { return P_; }
+  Exec* exec() { return ex_; }
+
+  // MPS basis input: sector tables of B_0..B_bond / C_{bond+2}..C_L and the
+  // isometries of sites 0..bond-1 / bond+2..L-1 (host arrays).
+  void load_left(int site, const Sectors& out, const std::vector<const double*>& mats);
+  void load_right(int site, const Sectors& out, const std::vector<const double*>& mats);
+  void build_left_blocks(int upto);     // B_0 .. B_upto from the loaded left isometries
+  void build_right_blocks(int downto);  // C_L .. C_downto
+
+  // bond workspace
+  void prepare_bond(int bond);
+  int bond() const { return bond_; }
+  const std::vector<int64_t>& layout() const { return lay_; }   // rows of 7 ints (see ABI)
+  int64_t psi_size() const { return psi_n_; }
+  const BondStats& stats() const { return st_; }
+
+  void sigma(const double* psi, double* sig);                 // device pointers, FP64 path
+  void sigma_precision(const double* psi, double* sig, int precision);
+  void diagonal(double* d);                                    // diag of H_eff (device)
+
+  // Davidson on the current bond; psi in/out (device).  Returns energy.
+  double davidson(double* psi, double tol, int max_iter, int max_sub, int* iters_out, int refine);
+
+  // sweeps
+  void init_sweep_state();
+  std::vector<double> run_sweeps(int n, const int* Dsched, double tol);
+
+  // expose a block operator for tests
+  const Block& left_block(int n) const { return lb_[n]; }
+  const Block& right_block(int m) const { return rb_[m]; }
+
+  // reduced density matrices at the current bond: g1 += <lam|E|psi>, g2 += ...
+  void rdm(const double* lam, const double* psi, double* g1, double* g2);
+
+  double last_energy = 0.0;
+  double last_rnorm = 0.0;
+  struct StepLog { int sweep, bond, ltr; double energy; int iters; };
+  std::vector<StepLog> sweep_log_;
+  void set_D(int D) { P_.D = D; }
+  void set_precision(int p) { P_.precision = p; }
+
+ private:
+  Problem P_;
+  Exec* ex_;
+  std::vector<Block> lb_, rb_;
+  std::vector<Iso> liso_, riso_;
+  int bond_ = -1;
+  int lb_sec_known_ = 0;
+  Enlarged EL_, ER_;
+  OpSet EopsL_, EopsR_;
+  std::vector<int64_t> lay_;
+  std::vector<int64_t> psi_off_;       // per coarse L' sector: offset of psi block or -1
+  std::vector<int> psi_rcoarse_;       // per coarse L' sector: coarse R' sector or -1
+  int64_t psi_n_ = 0;
+  BondStats st_;
+  // sigma plan
+  struct Chunk { int plan1 = -1; int plan2 = -1; };
+  std::vector<Chunk> chunks_;
+  int plan_hl_ = -1;
+  double* xbuf_ = nullptr;
+  double* psi_in_ = nullptr;
+  double* sig_out_ = nullptr;
+  int diag_plan_ = -1;
+  std::vector<DiagTask> diag_tasks_;
+  double* diag_l_ = nullptr;
+  double* diag_r_ = nullptr;
+  double* diag_ = nullptr;
+  // sweep state
+  double* psi_cur_ = nullptr;
+  int64_t psi_cur_cap_ = 0;
+
+  void free_opset(OpSet& s);
+  void alloc_opset(OpSet& s);
+  void enlarge(bool left, const Block& blk, int site, Enlarged& E, OpSet& out);
+  void renormalize(bool left, const Enlarged& E, const OpSet& eops, const Iso& iso, Block& out);
+  void build_sigma_plan();
+  void free_bond();
+  void truncate_and_move(bool left_to_right, int D, double* trunc_w);
+};
+
+// site matrices
+Site4 site_cdag(int sigma);
+Site4 site_mul(const Site4& x, const Site4& y);
+Site4 site_T(const Site4& x);
+Site4 site_axpy(const Site4& x, double c, const Site4& y);  // x + c y
+
+}  // namespace dmrg

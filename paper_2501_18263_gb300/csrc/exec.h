@@ -1,0 +1,96 @@
+// Numerical primitives the DMRG host core drives.  The product library
+// implements them with sm_103a kernels (exec_cuda.cu); every pointer handed to
+// them is a device pointer owned by the engine's arenas.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace dmrg {
+
+// dst[r, c] (+)= sum_t coef_t * src_t[r, c]   (mode 0: src row-major, 1: src^T, 2: identity)
+struct KronTask {
+  const double* src;
+  int src_ld;
+  int mode;
+  double coef;
+};
+struct KronGroup {
+  double* dst;
+  int ld, rows, cols;
+  int t0, t1;        // task range in the task array
+  int accumulate;    // 0: dst = sum, 1: dst += sum
+};
+
+// C = alpha * sum_seg op(A_seg) op(B_seg)  (+ C if accumulate)
+// op(A) is M x K: ta = 0 -> A[m*lda + k], ta = 1 -> A[k*lda + m]
+// op(B) is K x N: tb = 0 -> B[k*ldb + n], tb = 1 -> B[n*ldb + k]
+struct GemmSeg {
+  const double* A;
+  const double* B;
+  int lda, ldb, K, ta, tb;
+};
+struct GemmProb {
+  double* C;
+  int ldc, M, N;
+  int s0, s1;        // segment range
+  double alpha;
+  int accumulate;
+};
+
+// element-wise diagonal extraction: dst[i * dst_stride] = coef * (src ? src[i*(ld+1)] : 1)
+struct DiagTask {
+  const double* src;
+  int ld, n;
+  double* dst;
+  int64_t dst_stride;
+  double coef;
+};
+
+class Exec {
+ public:
+  virtual ~Exec() {}
+  virtual void* alloc(size_t bytes) = 0;
+  virtual void release(void* p) = 0;
+  virtual void zero(void* p, size_t bytes) = 0;
+  virtual void h2d(void* d, const void* h, size_t bytes) = 0;
+  virtual void d2h(void* h, const void* d, size_t bytes) = 0;
+  virtual void d2d(void* d, const void* s, size_t bytes) = 0;
+  virtual void sync() = 0;
+
+  // grouped element-wise Kronecker accumulation (operator blocking)
+  virtual void kron(const std::vector<KronGroup>& g, const std::vector<KronTask>& t) = 0;
+  // grouped, segmented FP64 GEMM (one-shot upload)
+  virtual void gemm(const std::vector<GemmProb>& p, const std::vector<GemmSeg>& s) = 0;
+  // persistent plans (uploaded once, replayed during Davidson)
+  virtual int gemm_plan(const std::vector<GemmProb>& p, const std::vector<GemmSeg>& s) = 0;
+  virtual void gemm_run(int plan) = 0;
+  virtual void plan_free(int plan) = 0;
+  virtual void diag(const std::vector<DiagTask>& t) = 0;
+
+  // dense FP64 vector kernels on length-n vectors stored with a row stride
+  // out[i*ldo + j] = sum_e V[i*ldv + e] * X[j*ldx + e]     (i < m, j < k)
+  virtual void mdot(const double* V, int64_t ldv, int m, const double* X, int64_t ldx, int k,
+                    int64_t n, double* out, int ldo) = 0;
+  // Y_j = beta * Y_j + alpha * sum_i C[i*ldc + j] * V_i     (C is a device matrix)
+  virtual void lincomb(const double* V, int64_t ldv, int m, const double* C, int ldc, int k,
+                       int64_t n, double* Y, int64_t ldy, double alpha, double beta) = 0;
+  // y += alpha * s[0] * x   (s is a device scalar)
+  virtual void axpy_dev(const double* x, double* y, int64_t n, const double* s, double alpha) = 0;
+  // t = r / (theta - diag), |theta - diag| floored at floor (theta device scalar)
+  virtual void precond(const double* r, const double* diag, const double* theta, int64_t n,
+                       double* t, double floor) = 0;
+  // x *= 1 / sqrt(nrm2[0])
+  virtual void normalize(double* x, int64_t n, const double* nrm2) = 0;
+  // lowest eigenpair of the symmetric m x m matrix whose upper triangle is in H (ld ldh):
+  // theta[0] = eigenvalue, y[0..m) = eigenvector
+  virtual void ritz(const double* H, int ldh, int m, double* theta, double* y) = 0;
+  // batched symmetric eigen-decomposition (cyclic Jacobi, FP64): A_b is n_b x n_b
+  // (ld = n_b, destroyed), w_b ascending eigenvalues, Z_b eigenvectors as columns (ld n_b)
+  virtual void syev(const std::vector<double*>& A, const std::vector<double*>& w,
+                    const std::vector<double*>& Z, const std::vector<int>& n) = 0;
+};
+
+Exec* make_cuda_exec(void* stream, int precision_mode);
+
+}  // namespace dmrg
