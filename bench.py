@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the two-site DMRG Davidson sigma step on GB300.
+
+One step = one sigma = H_eff psi at the centre bond (stage-1 and stage-2 block
+GEMMs over all normal/complementary operator terms, the local terms and the
+scatter into sigma), with the renormalised operators resident in HBM.
+Default workload: L = 32 orbitals, 16 alpha + 16 beta electrons, D = 2048,
+seeded synthetic integrals (seed 3), seeded random block-sparse MPS basis.
+
+    python bench.py [--gpus N --steps K --warmup W] [--precision fp64|mixed]
+    python bench.py --impl reference        # the CPU oracle on the host cores
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun), every rank runs an
+independent replica of the workload (weak scaling, no collective on the data
+path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sigma TFLOP/s & sweep time, L=32 D=2048, mixed vs FP64 at |dE|<=1e-6 Eh"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=32)
+    ap.add_argument("--na", type=int, default=None)
+    ap.add_argument("--nb", type=int, default=None)
+    ap.add_argument("--D", type=int, default=2048)
+    ap.add_argument("--bond", type=int, default=None)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--cpu-sample", default="12,6,6,256", help="L,na,nb,D of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    a.na = a.L // 2 if a.na is None else a.na
+    a.nb = a.L // 2 if a.nb is None else a.nb
+    a.bond = a.L // 2 - 1 if a.bond is None else a.bond
+    return a
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(args, flops_of):
+    """The oracle (projected sigma through the FCI space) timed on the host cores on a bounded sample."""
+    import oracle as O
+    from paper_2501_18263_gb300 import inputs as I
+    L, na, nb, D = (int(x) for x in args.cpu_sample.split(","))
+    bond = L // 2 - 1
+    t, v = I.synthetic_integrals(L, args.seed)
+    bp = I.bond_problem(L, na, nb, D, bond, seed=args.seed + 1)
+    flops = flops_of(t, v, na, nb, D, bp, bond)
+    O.build()
+    t0 = time.perf_counter()
+    O.projected_sigma(t, v, na, nb, bp, bp.psi)
+    dt = time.perf_counter() - t0
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one projected sigma (FCI embedding, fci.c) at the centre bond of L={L}, {na}a+{nb}b, "
+                      f"D={D}, same integral generator; rate = that bond's algorithmic sigma flops / oracle seconds",
+            "seconds": dt}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2501_18263_gb300 import binding as B
+    from paper_2501_18263_gb300 import inputs as I
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+    prec = B.PREC_FP64 if args.precision == "fp64" else B.PREC_MIXED_BF16
+
+    t_setup = time.perf_counter()
+    t, v = I.synthetic_integrals(args.L, args.seed)
+    bp = I.bond_problem(args.L, args.na, args.nb, args.D, args.bond, seed=args.seed + 1)
+    d = B.Dmrg(t, v, args.na, args.nb, D=args.D, precision=prec, seed=args.seed, stream=stream.cuda_stream)
+    d.load_bond_problem(bp)
+    d.prepare(args.bond)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    st = d.stats()
+    flops = st["flops_stage1"] + st["flops_stage2"]
+    n = st["psi_size"]
+    psi = torch.tensor(B.pack_psi(bp.psi), dtype=torch.float64, device=dev)
+    sig = torch.empty_like(psi)
+
+    for _ in range(args.warmup):
+        d.sigma(args.bond, psi.data_ptr(), sig.data_ptr())
+    torch.cuda.synchronize()
+
+    clk = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    d.profile_start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        d.sigma(args.bond, psi.data_ptr(), sig.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = d.profile_stop()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = flops * world / (ms * 1e-3) / 1e12
+
+    # end to end through the public host-buffer entry point
+    psi_h = np.ascontiguousarray(B.pack_psi(bp.psi))
+    d.sigma_host(args.bond, psi_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ke = max(1, args.steps)
+    for _ in range(ke):
+        d.sigma_host(args.bond, psi_h)
+    e2e_s = (time.perf_counter() - t0) / ke
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    pk, pk_kind = peaks()
+    if prec == B.PREC_FP64:
+        key = "gemm_f64"
+        mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = 152 * 2 * 2 * mhz * 1e6 / 1e12   # 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x max clock
+        bound, unit, peak_kind = "alu", "TFLOP/s", "derived (152 SM x 2 DFMA/clk x 2 flop x sm_max_mhz)"
+    else:
+        key = "gemm_bf16x"
+        peak = pk["bf16_tflops"]
+        bound, unit, peak_kind = "tensor", "TFLOP/s", pk_kind
+    kms = prof[key]["ms"] / args.steps if prof[key]["launches"] else None
+    achieved = flops / (kms * 1e-3) / 1e12 if kms else None
+    launches = sum(c["launches"] for c in prof.values())
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "TFLOP/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if prec == B.PREC_FP64 else "bf16x3-split/f32acc",
+        "data": "synthetic (seeded integrals and random block-sparse MPS basis)",
+        "config": {
+            "workload": f"sigma step at the centre bond (k={args.bond}) of L={args.L}, {args.na}a+{args.nb}b, "
+                        f"D={args.D}, synthetic integrals seed {args.seed}",
+            "L": args.L, "n_alpha": args.na, "n_beta": args.nb, "D": args.D, "bond": args.bond,
+            "precision": args.precision, "psi_size": n, "terms": st["n_terms"],
+            "flops_per_sigma": flops, "operator_bytes": st["op_bytes"],
+            "l2": "inputs larger than L2 (renormalised operators %.1f GB resident)" % (st["op_bytes"] / 1e9),
+            "setup_s": round(t_setup, 1),
+        },
+        "clocks": clocks,
+        "e2e": {"value": round(flops / e2e_s / 1e12, 4), "unit": "TFLOP/s",
+                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
+        "gpu_launches": launches,
+        "roofline": {"bound": bound, "achieved": round(achieved, 4) if achieved else None,
+                     "peak": round(peak, 3), "unit": unit,
+                     "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                     "kernel": key, "peak_source": peak_kind,
+                     "kernel_ms_per_step": round(kms, 3) if kms else None},
+        "profile_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        def flops_of(t_, v_, na_, nb_, D_, bp_, bond_):
+            dd = B.Dmrg(t_, v_, na_, nb_, D=D_, stream=stream.cuda_stream)
+            dd.load_bond_problem(bp_)
+            dd.prepare(bond_)
+            s_ = dd.stats()
+            dd.close()
+            return s_["flops_stage1"] + s_["flops_stage2"]
+        try:
+            out["cpu_baseline"] = cpu_baseline(args, flops_of)
+        except Exception as e:  # pragma: no cover
+            out["cpu_baseline"] = {"error": str(e)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    d.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, same metric and unit (bounded sample per step)."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2501_18263_gb300 import inputs as I
+    L, na, nb, D = (int(x) for x in args.cpu_sample.split(","))
+    bond = L // 2 - 1
+    t, v = I.synthetic_integrals(L, args.seed)
+    bp = I.bond_problem(L, na, nb, D, bond, seed=args.seed + 1)
+    flops = None
+    try:  # algorithmic flops of the sample bond from the method's own count
+        import torch
+        from paper_2501_18263_gb300 import binding as B
+        if torch.cuda.is_available():
+            dd = B.Dmrg(t, v, na, nb, D=D, stream=torch.cuda.current_stream().cuda_stream)
+            dd.load_bond_problem(bp)
+            dd.prepare(bond)
+            s_ = dd.stats()
+            flops = s_["flops_stage1"] + s_["flops_stage2"]
+            dd.close()
+    except Exception:
+        flops = None
+    O.build()
+    for _ in range(args.warmup and 1):
+        O.projected_sigma(t, v, na, nb, bp, bp.psi)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.projected_sigma(t, v, na, nb, bp, bp.psi)
+    dt = (time.perf_counter() - t0) / args.steps
+    val = flops / dt / 1e12 if flops else None
+    sample = (f"one projected sigma per step (FCI embedding, fci.c) at the centre bond of L={L}, {na}a+{nb}b, D={D}, "
+              f"same integral generator")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": sample, "L": L, "n_alpha": na, "n_beta": nb, "D": D, "bond": bond},
+        "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "sample": sample, "value": val},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -149,6 +149,13 @@ dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi_
  * device kernel launches of one sigma. */
 dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out8);
 
+/* Kernel timing with CUDA events on the handle's stream (this library's
+ * kernels only).  mode = 1: reset counters and start; mode = 0: stop and write
+ * out12[2c] = milliseconds and out12[2c+1] = launches for the kernel classes
+ * c = 0 FP64 GEMM, 1 blocking (kron), 2 vector, 3 Jacobi eigen, 4 split-BF16
+ * tensor-core GEMM, 5 split/pack.  out12 may be NULL when mode = 1. */
+dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out12);
+
 void dmrg_destroy(dmrg_handle* h);
 
 /* Thread-local message of the last failing call (empty string if none). */

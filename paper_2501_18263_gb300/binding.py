@@ -19,7 +19,8 @@ PREC_FP64, PREC_MIXED_BF16 = 0, 1
 
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
            "dmrg_sigma_host", "dmrg_davidson", "dmrg_sweep", "dmrg_sigma_backward", "dmrg_stats",
-           "dmrg_destroy", "dmrg_last_error"]
+           "dmrg_profile", "dmrg_destroy", "dmrg_last_error"]
+PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "jacobi", "gemm_bf16x", "split"]
 
 
 class DmrgError(RuntimeError):
@@ -58,6 +59,7 @@ def load_library(path: str | None = None):
         "dmrg_sweep": ([vp, i32, ip, f64, dp], ctypes.c_int),
         "dmrg_sigma_backward": ([vp, i32, vp, vp, vp, vp], ctypes.c_int),
         "dmrg_stats": ([vp, i64p], ctypes.c_int),
+        "dmrg_profile": ([vp, i32, dp], ctypes.c_int),
         "dmrg_destroy": ([vp], None),
         "dmrg_last_error": ([], ctypes.c_char_p),
     }
@@ -162,6 +164,14 @@ class Dmrg:
         self._check(self.lib.dmrg_sigma_backward(self.h, bond, ctypes.c_void_p(int(psi_ptr)),
                                                  ctypes.c_void_p(int(lam_ptr)), ctypes.c_void_p(int(g1_ptr)),
                                                  ctypes.c_void_p(int(g2_ptr))))
+
+    def profile_start(self):
+        self._check(self.lib.dmrg_profile(self.h, 1, None))
+
+    def profile_stop(self):
+        o = np.zeros(12)
+        self._check(self.lib.dmrg_profile(self.h, 0, _dp(o)))
+        return {c: {"ms": float(o[2 * i]), "launches": int(o[2 * i + 1])} for i, c in enumerate(PROFILE_CLASSES)}
 
     def stats(self):
         o = np.zeros(8, dtype=np.int64)

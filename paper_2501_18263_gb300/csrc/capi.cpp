@@ -289,6 +289,15 @@ dmrg_status dmrg_stats(dmrg_handle* h, int64_t* o) {
   });
 }
 
+dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out) {
+  return guard([&]() -> dmrg_status {
+    if (!h) return fail(DMRG_ERR_ARG, "null handle");
+    if (mode != 0 && mode != 1) return fail(DMRG_ERR_ARG, "mode must be 0 or 1");
+    h->eng->exec()->profile(mode, out);
+    return DMRG_OK;
+  });
+}
+
 void dmrg_destroy(dmrg_handle* h) {
   try {
     if (h) {

@@ -148,6 +148,9 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
   double* W = static_cast<double*>(ex_->alloc(size_t(max_sub) * n * sizeof(double)));
   double* x = static_cast<double*>(ex_->alloc(n * sizeof(double)));
   double* wx = static_cast<double*>(ex_->alloc(n * sizeof(double)));
+  double* xp = static_cast<double*>(ex_->alloc(n * sizeof(double)));   // previous Ritz vector
+  double* wxp = static_cast<double*>(ex_->alloc(n * sizeof(double)));
+  bool have_prev = false;
   double* r = static_cast<double*>(ex_->alloc(n * sizeof(double)));
   double* t = static_cast<double*>(ex_->alloc(n * sizeof(double)));
   double* diag = static_cast<double*>(ex_->alloc(n * sizeof(double)));
@@ -180,6 +183,11 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
   bool refined_done = (prec == 0 || !refine);
   for (;; ++it) {
     ex_->ritz(Hs, lds, m, theta, y);
+    if (it > 0) {
+      std::swap(x, xp);
+      std::swap(wx, wxp);
+      have_prev = true;
+    }
     ex_->lincomb(V, n, m, y, 1, 1, n, x, n, 1.0, 0.0);
     ex_->lincomb(W, n, m, y, 1, 1, n, wx, n, 1.0, 0.0);
     ex_->d2d(r, wx, n * sizeof(double));
@@ -204,12 +212,39 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
     }
     if (conv || it >= max_iter) break;
     if (m == max_sub) {
-      // restart with the current Ritz vector
+      // restart with the current Ritz vector and the part of the previous one
+      // orthogonal to it (two-vector restart)
       ex_->d2d(V, x, n * sizeof(double));
       ex_->d2d(W, wx, n * sizeof(double));
       ex_->zero(Hs, size_t(lds) * lds * sizeof(double));
       ex_->d2d(Hs, theta, sizeof(double));
       m = 1;
+      if (have_prev) {
+        double* V1 = V + n;
+        double* W1 = W + n;
+        ex_->mdot(x, n, 1, xp, n, 1, n, cf, 1);
+        ex_->d2d(V1, xp, n * sizeof(double));
+        ex_->axpy_dev(x, V1, n, cf, -1.0);
+        ex_->d2d(W1, wxp, n * sizeof(double));
+        ex_->axpy_dev(wx, W1, n, cf, -1.0);
+        ex_->mdot(V1, n, 1, V1, n, 1, n, nrm2, 1);
+        double pn2;
+        ex_->d2h(&pn2, nrm2, sizeof(double));
+        // keep the second direction only when it is well resolved (|xp - c x| > 1e-4),
+        // and orthogonalise it once more against x
+        if (pn2 > 1e-8) {
+          ex_->normalize(V1, n, nrm2);
+          ex_->normalize(W1, n, nrm2);
+          ex_->mdot(V, n, 1, V1, n, 1, n, cf, 1);
+          ex_->axpy_dev(V, V1, n, cf, -1.0);
+          ex_->axpy_dev(W, W1, n, cf, -1.0);
+          ex_->mdot(V1, n, 1, V1, n, 1, n, nrm2, 1);
+          ex_->normalize(V1, n, nrm2);
+          ex_->normalize(W1, n, nrm2);
+          ex_->mdot(V, n, 2, W1, n, 1, n, Hs + 1, lds);
+          m = 2;
+        }
+      }
     }
     ex_->precond(r, diag, theta, n, t, 1e-8);
     for (int pass = 0; pass < 2; ++pass) {
@@ -230,7 +265,7 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
   ex_->mdot(x, n, 1, x, n, 1, n, nrm2, 1);
   ex_->normalize(x, n, nrm2);
   ex_->d2d(psi, x, n * sizeof(double));
-  for (double* p : {V, W, x, wx, r, t, diag, small}) ex_->release(p);
+  for (double* p : {V, W, x, wx, xp, wxp, r, t, diag, small}) ex_->release(p);
   if (iters_out) *iters_out = it + 1;
   last_energy = th;
   last_rnorm = rnorm;

@@ -353,6 +353,8 @@ void Engine::build_sigma_plan() {
       }
     }
     plan_hl_ = P3.empty() ? -1 : ex_->gemm_plan(P3, S3);
+    st_.launches_per_sigma = (plan_hl_ >= 0 ? 1 : 0);
+    for (auto& c : chunks_) st_.launches_per_sigma += (c.plan1 >= 0 ? 1 : 0) + 1;
     st_.n_gemm_problems += int(P3.size());
     st_.n_gemm_segments += int(S3.size());
   }

@@ -89,7 +89,14 @@ class Exec {
   // (ld = n_b, destroyed), w_b ascending eigenvalues, Z_b eigenvectors as columns (ld n_b)
   virtual void syev(const std::vector<double*>& A, const std::vector<double*>& w,
                     const std::vector<double*>& Z, const std::vector<int>& n) = 0;
+
+  // kernel timing with events on the stream: mode 1 resets and starts, mode 0 stops
+  // and fills out[2*c] = milliseconds, out[2*c+1] = launches for each kernel class c
+  // (0 gemm_f64, 1 kron, 2 vector, 3 syev/ritz, 4 mixed gemm, 5 split/pack)
+  virtual void profile(int mode, double* out) = 0;
 };
+
+enum { PROF_GEMM = 0, PROF_KRON, PROF_VEC, PROF_EIG, PROF_MIXED, PROF_SPLIT, PROF_N };
 
 Exec* make_cuda_exec(void* stream, int precision_mode);
 

@@ -1,0 +1,634 @@
+// CUDA executor: the sm_103a kernels behind the host core's numerical steps.
+//   gemm_f64      grouped, segmented FP64 GEMM (the FP64 sigma / Ren / StVec path)
+//   kron          grouped Kronecker accumulation (operator blocking)
+//   mdot/lincomb  Davidson Gram-Schmidt and Ritz vectors (deterministic reductions)
+//   ritz/syev     cyclic Jacobi eigen-solvers for the Rayleigh-Ritz matrix and the
+//                 density matrices of the truncation
+// All work is ordered on one stream; allocations are stream-ordered.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../exec.h"
+#include "../exec_errors.h"
+
+namespace dmrg {
+
+#define CK(x)                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (x);                                                              \
+    if (e_ != cudaSuccess) {                                                           \
+      if (e_ == cudaErrorMemoryAllocation) throw OomError(std::string("CUDA: ") + cudaGetErrorString(e_)); \
+      throw CudaError(std::string(#x) + ": " + cudaGetErrorString(e_));               \
+    }                                                                                  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// grouped FP64 GEMM: one CTA per 64 x 64 output tile, K loop over all segments
+
+struct GemmTile {
+  int prob, m0, n0, pad;
+};
+
+constexpr int TM = 64, TN = 64, TK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmTile* __restrict__ tiles,
+                                                       const GemmProb* __restrict__ probs,
+                                                       const GemmSeg* __restrict__ segs) {
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmProb p = probs[tl.prob];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const int Mt = min(TM, p.M - tl.m0), Nt = min(TN, p.N - tl.n0);
+  for (int s = p.s0; s < p.s1; ++s) {
+    const GemmSeg g = segs[s];
+    for (int k0 = 0; k0 < g.K; k0 += TK) {
+      const int Kt = min(TK, g.K - k0);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = tid + 256 * r;
+        int m, k;
+        if (g.ta == 0) { m = i >> 4; k = i & 15; } else { m = i & 63; k = i >> 6; }
+        double a = 0.0;
+        if (m < Mt && k < Kt) {
+          const int64_t gm = tl.m0 + m, gk = k0 + k;
+          a = g.ta == 0 ? g.A[gm * g.lda + gk] : g.A[gk * g.lda + gm];
+        }
+        As[k][m] = a;
+        int n, kb;
+        if (g.tb == 0) { n = i & 63; kb = i >> 6; } else { n = i >> 4; kb = i & 15; }
+        double b = 0.0;
+        if (n < Nt && kb < Kt) {
+          const int64_t gn = tl.n0 + n, gk = k0 + kb;
+          b = g.tb == 0 ? g.B[gk * g.ldb + gn] : g.B[gn * g.ldb + gk];
+        }
+        Bs[kb][n] = b;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < TK; ++k) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = ty * 4 + i;
+    if (m >= Mt) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = tx * 4 + j;
+      if (n >= Nt) continue;
+      double* c = p.C + int64_t(tl.m0 + m) * p.ldc + tl.n0 + n;
+      const double v = p.alpha * acc[i][j];
+      *c = p.accumulate ? *c + v : v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// grouped Kronecker accumulation
+
+struct KronCta {
+  int group, e0;
+};
+constexpr int KRON_CHUNK = 1024;
+
+__global__ void __launch_bounds__(256) kron_kernel(const KronCta* __restrict__ ctas,
+                                                   const KronGroup* __restrict__ groups,
+                                                   const KronTask* __restrict__ tasks) {
+  const KronCta c = ctas[blockIdx.x];
+  const KronGroup g = groups[c.group];
+  const int n = g.rows * g.cols;
+  const int e1 = min(n, c.e0 + KRON_CHUNK);
+  for (int e = c.e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int r = e / g.cols, col = e - r * g.cols;
+    double acc = 0.0;
+    for (int t = g.t0; t < g.t1; ++t) {
+      const KronTask k = tasks[t];
+      double v;
+      if (k.mode == 0) v = k.src[int64_t(r) * k.src_ld + col];
+      else if (k.mode == 1) v = k.src[int64_t(col) * k.src_ld + r];
+      else v = (r == col) ? 1.0 : 0.0;
+      acc = fma(k.coef, v, acc);
+    }
+    double* d = g.dst + int64_t(r) * g.ld + col;
+    *d = g.accumulate ? *d + acc : acc;
+  }
+}
+
+__global__ void diag_kernel(const DiagTask* __restrict__ t, int nt) {
+  for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+    const DiagTask d = t[i];
+    for (int e = threadIdx.x; e < d.n; e += blockDim.x)
+      d.dst[e * d.dst_stride] = d.coef * (d.src ? d.src[int64_t(e) * (d.ld + 1)] : 1.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// vector kernels
+
+constexpr int MDOT_MAX = 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) mdot_partial(const double* __restrict__ V, int64_t ldv, int m,
+                                                    const double* __restrict__ X, int64_t ldx, int64_t n,
+                                                    double* __restrict__ part) {
+  const int j = blockIdx.y, b = blockIdx.x, nb = gridDim.x;
+  const int64_t e0 = n * b / nb, e1 = n * (b + 1) / nb;
+  double acc[MDOT_MAX];
+#pragma unroll
+  for (int i = 0; i < MDOT_MAX; ++i) acc[i] = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const double x = X[j * ldx + e];
+#pragma unroll
+    for (int i = 0; i < MDOT_MAX; ++i)
+      if (i < m) acc[i] = fma(V[i * ldv + e], x, acc[i]);
+  }
+  __shared__ double red[8][MDOT_MAX];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < MDOT_MAX; ++i) {
+    if (i >= m) break;
+    double s = warp_sum(acc[i]);
+    if (l == 0) red[w][i] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < m) {
+    double s = 0.0;
+    for (int ww = 0; ww < 8; ++ww) s += red[ww][threadIdx.x];
+    part[(int64_t(b) * gridDim.y + j) * MDOT_MAX + threadIdx.x] = s;
+  }
+}
+
+__global__ void mdot_final(const double* __restrict__ part, int nb, int m, int k, double* out, int ldo) {
+  const int t = threadIdx.x + blockIdx.x * blockDim.x;
+  if (t >= m * k) return;
+  const int i = t / k, j = t % k;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(int64_t(b) * k + j) * MDOT_MAX + i];
+  out[i * ldo + j] = s;
+}
+
+__global__ void lincomb_kernel(const double* __restrict__ V, int64_t ldv, int m, const double* __restrict__ C,
+                               int ldc, int k, int64_t n, double* Y, int64_t ldy, double alpha, double beta) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    for (int j = 0; j < k; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s = fma(C[i * ldc + j], V[i * ldv + e], s);
+      double* y = Y + j * ldy + e;
+      *y = (beta == 0.0 ? 0.0 : beta * *y) + alpha * s;
+    }
+}
+
+__global__ void axpy_dev_kernel(const double* __restrict__ x, double* y, int64_t n, const double* s, double alpha) {
+  const double a = alpha * s[0];
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    y[e] = fma(a, x[e], y[e]);
+}
+
+__global__ void precond_kernel(const double* __restrict__ r, const double* __restrict__ d, const double* th,
+                               int64_t n, double* t, double fl) {
+  const double theta = th[0];
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+    double den = theta - d[e];
+    if (fabs(den) < fl) den = den < 0 ? -fl : fl;
+    t[e] = r[e] / den;
+  }
+}
+
+__global__ void normalize_kernel(double* x, int64_t n, const double* nrm2) {
+  const double s = 1.0 / sqrt(nrm2[0]);
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    x[e] *= s;
+}
+
+// ---------------------------------------------------------------------------
+// cyclic Jacobi with the round-robin (tournament) pair ordering: n/2 disjoint
+// rotations per step are computed from the current matrix and applied together.
+
+template <bool SHARED>
+__device__ void jacobi_core(double* A, double* Z, int n, int ld, double* cs, int* pp, int* qq, double* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int ne = n + (n & 1);  // even count (dummy index ne-1 when n is odd)
+  for (int e = tid; e < n * n; e += nt) Z[(e / n) * ld + e % n] = (e / n == e % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    // convergence: off-diagonal Frobenius norm relative to the full norm
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, j = e % n;
+      const double a = A[i * ld + j];
+      tot += a * a;
+      if (i != j) off += a * a;
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if ((tid & 31) == 0) {
+      red[2 * (tid >> 5)] = off;
+      red[2 * (tid >> 5) + 1] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double o = 0, t = 0;
+      for (int w = 0; w < nt / 32; ++w) {
+        o += red[2 * w];
+        t += red[2 * w + 1];
+      }
+      red[64] = (o <= 1e-26 * t || t == 0.0) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const bool done = red[64] != 0.0;
+    __syncthreads();
+    if (done) break;
+    for (int step = 0; step < ne - 1; ++step) {
+      // pairs of the round-robin schedule
+      for (int k = tid; k < ne / 2; k += nt) {
+        int a, b;
+        if (k == 0) {
+          a = ne - 1;
+          b = step;
+        } else {
+          a = (step + k) % (ne - 1);
+          b = (step - k + ne - 1) % (ne - 1);
+        }
+        int p = min(a, b), q = max(a, b);
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          const double apq = A[p * ld + q];
+          if (apq != 0.0) {
+            const double app = A[p * ld + p], aqq = A[q * ld + q];
+            const double th = (aqq - app) / (2.0 * apq);
+            const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        pp[k] = p;
+        qq[k] = q;
+        cs[2 * k] = c;
+        cs[2 * k + 1] = s;
+      }
+      __syncthreads();
+      // columns: A <- A J, Z <- Z J
+      for (int e = tid; e < (ne / 2) * n; e += nt) {
+        const int k = e / n, row = e % n;
+        const int p = pp[k], q = qq[k];
+        if (q >= n) continue;
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        if (s == 0.0) continue;
+        const double ap = A[row * ld + p], aq = A[row * ld + q];
+        A[row * ld + p] = c * ap - s * aq;
+        A[row * ld + q] = s * ap + c * aq;
+        const double zp = Z[row * ld + p], zq = Z[row * ld + q];
+        Z[row * ld + p] = c * zp - s * zq;
+        Z[row * ld + q] = s * zp + c * zq;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < (ne / 2) * n; e += nt) {
+        const int k = e / n, col = e % n;
+        const int p = pp[k], q = qq[k];
+        if (q >= n) continue;
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        if (s == 0.0) continue;
+        const double ap = A[p * ld + col], aq = A[q * ld + col];
+        A[p * ld + col] = c * ap - s * aq;
+        A[q * ld + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// batched eigen-decomposition, one CTA per matrix (matrices in global memory)
+struct SyevJob {
+  double* A;
+  double* w;
+  double* Z;
+  int n, pad;
+};
+
+__global__ void __launch_bounds__(256) syev_kernel(const SyevJob* jobs, int* work_i, double* work_d, int maxn) {
+  const SyevJob jb = jobs[blockIdx.x];
+  const int n = jb.n;
+  extern __shared__ double sm[];
+  double* cs = sm;                              // 2 * ceil(n/2)+2
+  double* red = sm + maxn + 4;                  // 65
+  int* pp = reinterpret_cast<int*>(red + 72);
+  int* qq = pp + (maxn / 2 + 2);
+  jacobi_core<false>(jb.A, jb.Z, n, n, cs, pp, qq, red);
+  // sort ascending: rank of each diagonal element; permuted columns go through A
+  __syncthreads();
+  double* dg = reinterpret_cast<double*>(work_d) + int64_t(blockIdx.x) * maxn;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = jb.A[i * n + i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int r = 0;
+    const double di = dg[i];
+    for (int j = 0; j < n; ++j) {
+      const double dj = dg[j];
+      r += (dj < di) || (dj == di && j < i);
+    }
+    jb.w[r] = di;
+    for (int row = 0; row < n; ++row) jb.A[row * n + r] = jb.Z[row * n + i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) jb.Z[e] = jb.A[e];
+  (void)work_i;
+}
+
+// Rayleigh-Ritz of the Davidson subspace: lowest eigenpair of an m x m matrix (m <= 40)
+__global__ void __launch_bounds__(64) ritz_kernel(const double* H, int ldh, int m, double* theta, double* y) {
+  __shared__ double A[40 * 40];
+  __shared__ double Z[40 * 40];
+  __shared__ double cs[44];
+  __shared__ double red[72];
+  __shared__ int pp[22], qq[22];
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    A[i * m + j] = i <= j ? H[i * ldh + j] : H[j * ldh + i];
+  }
+  __syncthreads();
+  jacobi_core<true>(A, Z, m, m, cs, pp, qq, red);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int best = 0;
+    for (int i = 1; i < m; ++i)
+      if (A[i * m + i] < A[best * m + best]) best = i;
+    theta[0] = A[best * m + best];
+    // fix the sign: largest-magnitude component positive
+    int arg = 0;
+    for (int i = 1; i < m; ++i)
+      if (fabs(Z[i * m + best]) > fabs(Z[arg * m + best])) arg = i;
+    const double sg = Z[arg * m + best] < 0 ? -1.0 : 1.0;
+    for (int i = 0; i < m; ++i) y[i] = sg * Z[i * m + best];
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+class CudaExec : public Exec {
+  struct Mark {
+    cudaEvent_t a, b;
+    int cls;
+  };
+  bool prof_ = false;
+  std::vector<Mark> marks_;
+  std::vector<cudaEvent_t> pool_;
+  double acc_[2 * PROF_N] = {};
+  cudaEvent_t ev() {
+    if (pool_.empty()) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      return e;
+    }
+    cudaEvent_t e = pool_.back();
+    pool_.pop_back();
+    return e;
+  }
+  // bracket one launch with events when profiling
+  template <class F>
+  void launch(int cls, F&& f) {
+    if (!prof_) {
+      f();
+      CK(cudaGetLastError());
+      return;
+    }
+    Mark m{ev(), ev(), cls};
+    CK(cudaEventRecord(m.a, st_));
+    f();
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(m.b, st_));
+    marks_.push_back(m);
+    if (marks_.size() > 4096) drain();
+  }
+  void drain() {
+    if (marks_.empty()) return;
+    CK(cudaEventSynchronize(marks_.back().b));
+    for (auto& m : marks_) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, m.a, m.b));
+      acc_[2 * m.cls] += ms;
+      acc_[2 * m.cls + 1] += 1;
+      pool_.push_back(m.a);
+      pool_.push_back(m.b);
+    }
+    marks_.clear();
+  }
+
+ public:
+  void profile(int mode, double* out) override {
+    if (mode == 1) {
+      drain();
+      for (double& x : acc_) x = 0;
+      prof_ = true;
+    } else {
+      drain();
+      prof_ = false;
+      if (out)
+        for (int i = 0; i < 2 * PROF_N; ++i) out[i] = acc_[i];
+    }
+  }
+
+  CudaExec(void* stream, int prec) : st_(static_cast<cudaStream_t>(stream)), prec_(prec) {
+    CK(cudaGetDevice(&dev_));
+    CK(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev_));
+    CK(cudaMalloc(&part_, sizeof(double) * 1024 * MDOT_MAX * 4));
+  }
+  ~CudaExec() override {
+    try { drain(); } catch (...) {}
+    for (auto& m : marks_) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+    for (auto e : pool_) cudaEventDestroy(e);
+    for (auto& p : plans_) free_plan_mem(p);
+    cudaFree(part_);
+  }
+  void* alloc(size_t b) override {
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, b ? b : 8, st_);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw OomError("device allocation of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    return p;
+  }
+  void release(void* p) override {
+    if (p) CK(cudaFreeAsync(p, st_));
+  }
+  void zero(void* p, size_t b) override {
+    if (b) CK(cudaMemsetAsync(p, 0, b, st_));
+  }
+  void h2d(void* d, const void* h, size_t b) override {
+    if (b) CK(cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, st_));
+  }
+  void d2h(void* h, const void* d, size_t b) override {
+    if (b) {
+      CK(cudaMemcpyAsync(h, d, b, cudaMemcpyDeviceToHost, st_));
+      CK(cudaStreamSynchronize(st_));
+    }
+  }
+  void d2d(void* d, const void* s, size_t b) override {
+    if (b && d != s) CK(cudaMemcpyAsync(d, s, b, cudaMemcpyDeviceToDevice, st_));
+  }
+  void sync() override { CK(cudaStreamSynchronize(st_)); }
+
+  template <class T>
+  T* upload(const std::vector<T>& v) {
+    T* d = static_cast<T*>(alloc(sizeof(T) * std::max<size_t>(v.size(), 1)));
+    h2d(d, v.data(), sizeof(T) * v.size());
+    return d;
+  }
+
+  void kron(const std::vector<KronGroup>& g, const std::vector<KronTask>& t) override {
+    if (g.empty()) return;
+    std::vector<KronCta> ctas;
+    for (size_t i = 0; i < g.size(); ++i)
+      for (int e = 0; e < g[i].rows * g[i].cols; e += KRON_CHUNK) ctas.push_back(KronCta{int(i), e});
+    KronGroup* dg = upload(g);
+    KronTask* dt = upload(t);
+    KronCta* dc = upload(ctas);
+    for (size_t c0 = 0; c0 < ctas.size(); c0 += (1u << 30)) {
+      unsigned nb = unsigned(std::min<size_t>(ctas.size() - c0, 1u << 30));
+      launch(PROF_KRON, [&] { kron_kernel<<<nb, 256, 0, st_>>>(dc + c0, dg, dt); });
+    }
+    release(dg);
+    release(dt);
+    release(dc);
+  }
+
+  struct Plan {
+    GemmTile* tiles = nullptr;
+    GemmProb* probs = nullptr;
+    GemmSeg* segs = nullptr;
+    int ntiles = 0;
+    bool live = false;
+  };
+
+  int gemm_plan(const std::vector<GemmProb>& p, const std::vector<GemmSeg>& s) override {
+    Plan pl;
+    std::vector<GemmTile> tiles;
+    for (size_t i = 0; i < p.size(); ++i)
+      for (int m0 = 0; m0 < p[i].M; m0 += TM)
+        for (int n0 = 0; n0 < p[i].N; n0 += TN) tiles.push_back(GemmTile{int(i), m0, n0, 0});
+    pl.ntiles = int(tiles.size());
+    pl.tiles = upload(tiles);
+    pl.probs = upload(p);
+    pl.segs = upload(s);
+    pl.live = true;
+    for (size_t i = 0; i < plans_.size(); ++i)
+      if (!plans_[i].live) {
+        plans_[i] = pl;
+        return int(i);
+      }
+    plans_.push_back(pl);
+    return int(plans_.size() - 1);
+  }
+  void gemm_run(int id) override {
+    Plan& pl = plans_.at(id);
+    if (!pl.ntiles) return;
+    launch(PROF_GEMM, [&] { gemm_f64_kernel<<<pl.ntiles, 256, 0, st_>>>(pl.tiles, pl.probs, pl.segs); });
+  }
+  void free_plan_mem(Plan& p) {
+    if (!p.live) return;
+    cudaFreeAsync(p.tiles, st_);
+    cudaFreeAsync(p.probs, st_);
+    cudaFreeAsync(p.segs, st_);
+    p.live = false;
+  }
+  void plan_free(int id) override { free_plan_mem(plans_.at(id)); }
+  void gemm(const std::vector<GemmProb>& p, const std::vector<GemmSeg>& s) override {
+    if (p.empty()) return;
+    int id = gemm_plan(p, s);
+    gemm_run(id);
+    plan_free(id);
+  }
+  void diag(const std::vector<DiagTask>& t) override {
+    if (t.empty()) return;
+    DiagTask* d = upload(t);
+    launch(PROF_VEC, [&] { diag_kernel<<<std::min<size_t>(t.size(), 65535), 128, 0, st_>>>(d, int(t.size())); });
+    release(d);
+  }
+
+  int grid_for(int64_t n) const { return int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, int64_t(nsm_) * 8))); }
+
+  void mdot(const double* V, int64_t ldv, int m, const double* X, int64_t ldx, int k, int64_t n, double* out,
+            int ldo) override {
+    if (k > 4) throw std::runtime_error("mdot: at most 4 right-hand vectors");
+    for (int i0 = 0; i0 < m; i0 += MDOT_MAX) {
+      const int mm = std::min(MDOT_MAX, m - i0);
+      const int nb = int(std::max<int64_t>(1, std::min<int64_t>((n + 4095) / 4096, 1024 / std::max(1, k))));
+      launch(PROF_VEC, [&] { mdot_partial<<<dim3(nb, k), 256, 0, st_>>>(V + i0 * ldv, ldv, mm, X, ldx, n, part_); });
+      launch(PROF_VEC, [&] { mdot_final<<<(mm * k + 127) / 128, 128, 0, st_>>>(part_, nb, mm, k, out + i0 * ldo, ldo); });
+    }
+  }
+  void lincomb(const double* V, int64_t ldv, int m, const double* C, int ldc, int k, int64_t n, double* Y,
+               int64_t ldy, double alpha, double beta) override {
+    launch(PROF_VEC, [&] { lincomb_kernel<<<grid_for(n), 256, 0, st_>>>(V, ldv, m, C, ldc, k, n, Y, ldy, alpha, beta); });
+  }
+  void axpy_dev(const double* x, double* y, int64_t n, const double* s, double alpha) override {
+    launch(PROF_VEC, [&] { axpy_dev_kernel<<<grid_for(n), 256, 0, st_>>>(x, y, n, s, alpha); });
+  }
+  void precond(const double* r, const double* d, const double* th, int64_t n, double* t, double fl) override {
+    launch(PROF_VEC, [&] { precond_kernel<<<grid_for(n), 256, 0, st_>>>(r, d, th, n, t, fl); });
+  }
+  void normalize(double* x, int64_t n, const double* nrm2) override {
+    launch(PROF_VEC, [&] { normalize_kernel<<<grid_for(n), 256, 0, st_>>>(x, n, nrm2); });
+  }
+  void ritz(const double* H, int ldh, int m, double* theta, double* y) override {
+    if (m > 40) throw std::runtime_error("ritz: subspace larger than 40");
+    launch(PROF_EIG, [&] { ritz_kernel<<<1, 64, 0, st_>>>(H, ldh, m, theta, y); });
+  }
+  void syev(const std::vector<double*>& A, const std::vector<double*>& w, const std::vector<double*>& Z,
+            const std::vector<int>& n) override {
+    if (A.empty()) return;
+    std::vector<SyevJob> jobs;
+    int maxn = 2;
+    for (size_t i = 0; i < A.size(); ++i) {
+      jobs.push_back(SyevJob{A[i], w[i], Z[i], n[i], 0});
+      maxn = std::max(maxn, n[i] + 2);
+    }
+    SyevJob* dj = upload(jobs);
+    double* wd = static_cast<double*>(alloc(sizeof(double) * size_t(maxn) * jobs.size()));
+    size_t smem = sizeof(double) * (maxn + 4 + 72) + sizeof(int) * 2 * (maxn / 2 + 2);
+    if (smem > 48 * 1024) CK(cudaFuncSetAttribute(syev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    launch(PROF_EIG, [&] { syev_kernel<<<unsigned(jobs.size()), 256, smem, st_>>>(dj, nullptr, wd, maxn); });
+    release(dj);
+    release(wd);
+  }
+
+ private:
+  cudaStream_t st_;
+  int prec_;
+  int dev_ = 0, nsm_ = 148;
+  double* part_ = nullptr;
+  std::vector<Plan> plans_;
+};
+
+Exec* make_cuda_exec(void* stream, int precision_mode) { return new CudaExec(stream, precision_mode); }
+
+}  // namespace dmrg
