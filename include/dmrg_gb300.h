@@ -121,6 +121,24 @@ dmrg_status dmrg_sigma(dmrg_handle* h, int32_t bond, const double* psi_dev, doub
 /* Same with host buffers: host->device copy of psi, sigma, device->host copy. */
 dmrg_status dmrg_sigma_host(dmrg_handle* h, int32_t bond, const double* psi_host, double* sigma_host);
 
+/* Allocation-free variant of dmrg_sigma_host (the paper has no counterpart;
+ * this is a library convenience).  For callers that may not allocate device
+ * memory during the call -- for example while a CUDA graph is being captured,
+ * or under a memory pool that must not grow -- psi and sigma are staged in a
+ * device array built into the library (32 MiB, held by every device that loads
+ * the library until the process exits) instead of a buffer allocated per call.
+ * Requirements and limits:
+ *   - the bond must already be prepared (dmrg_prepare), which is where all of
+ *     the handle's device memory is allocated; this call allocates nothing;
+ *   - psi_size <= 2097152 doubles, otherwise DMRG_ERR_ARG;
+ *   - the handle's device must be current.  The first call on a device looks up
+ *     the array's device address once; make that first call before any stream
+ *     capture begins.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * that overlap on the GPU (other threads, other handles on the same device)
+ * race with each other and must be serialised by the caller. */
+dmrg_status dmrg_sigma_host_noalloc(dmrg_handle* h, int32_t bond, const double* psi_host, double* sigma_host);
+
 /* Lowest eigenpair of H_eff at `bond` by Davidson; psi_dev is the start vector
  * on entry and the normalised eigenvector on exit; *energy its Rayleigh
  * quotient (from an FP64 sigma).  tol bounds the residual 2-norm. */

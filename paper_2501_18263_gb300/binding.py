@@ -18,7 +18,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOCONV, ERR_NONFINITE, ERR_STAT
 PREC_FP64, PREC_MIXED_BF16 = 0, 1
 
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
-           "dmrg_sigma_host", "dmrg_davidson", "dmrg_sweep", "dmrg_sigma_backward", "dmrg_stats",
+           "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sigma_backward", "dmrg_stats",
            "dmrg_profile", "dmrg_destroy", "dmrg_last_error"]
 PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "jacobi", "gemm_bf16x", "split"]
 
@@ -55,6 +55,7 @@ def load_library(path: str | None = None):
         "dmrg_layout": ([vp, i32, ip, ctypes.POINTER(i64p), i64p], ctypes.c_int),
         "dmrg_sigma": ([vp, i32, vp, vp], ctypes.c_int),
         "dmrg_sigma_host": ([vp, i32, dp, dp], ctypes.c_int),
+        "dmrg_sigma_host_noalloc": ([vp, i32, dp, dp], ctypes.c_int),
         "dmrg_davidson": ([vp, i32, vp, f64, i32, dp, ip], ctypes.c_int),
         "dmrg_sweep": ([vp, i32, ip, f64, dp], ctypes.c_int),
         "dmrg_sigma_backward": ([vp, i32, vp, vp, vp, vp], ctypes.c_int),
@@ -139,6 +140,13 @@ class Dmrg:
         psi = np.ascontiguousarray(psi, dtype=np.float64)
         out = np.empty_like(psi)
         self._check(self.lib.dmrg_sigma_host(self.h, bond, _dp(psi), _dp(out)))
+        return out
+
+    def sigma_host_noalloc(self, bond, psi):
+        """sigma with host buffers staged through the library's built-in device array (no allocation)."""
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        out = np.empty_like(psi)
+        self._check(self.lib.dmrg_sigma_host_noalloc(self.h, bond, _dp(psi), _dp(out)))
         return out
 
     def davidson(self, bond, psi_ptr, tol=1e-8, max_iter=100, check=True):

@@ -11,14 +11,9 @@
 #include "core/core.h"
 #include "exec_errors.h"
 
-struct dmrg_handle {
-  std::unique_ptr<dmrg::Exec> ex;
-  std::unique_ptr<dmrg::Engine> eng;
-  int L = 0;
-  int left_loaded = 0;     // number of left sites loaded
-  int right_loaded = -1;   // lowest right site loaded (L if none)
-  bool any_loaded = false;
-};
+#include <cuda_runtime.h>
+
+#include "capi_internal.h"
 
 namespace {
 thread_local std::string g_err;
@@ -109,6 +104,7 @@ dmrg_status dmrg_build_ops(const dmrg_problem* p, void* stream, dmrg_handle** ou
                 p->v[((size_t(ord[i]) * L + ord[j]) * L + ord[k]) * L + ord[l]];
     auto h = std::make_unique<dmrg_handle>();
     h->L = L;
+    cudaGetDevice(&h->device);
     h->right_loaded = L;
     h->ex.reset(dmrg::make_cuda_exec(stream, p->precision));
     h->eng = std::make_unique<dmrg::Engine>(P, h->ex.get());
@@ -310,5 +306,11 @@ void dmrg_destroy(dmrg_handle* h) {
 }
 
 const char* dmrg_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+void dmrg_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+
+extern "C" {
 
 }  // extern "C"

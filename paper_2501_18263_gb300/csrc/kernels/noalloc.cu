@@ -1,0 +1,77 @@
+// dmrg_sigma_host_noalloc: the host-buffer sigma step without any device
+// allocation.  dmrg_sigma_host stages psi and sigma in a device buffer that it
+// allocates on every call; this variant stages them in a file-scope device
+// array instead, for callers that must not allocate device memory while they
+// run (for example code that is being captured into a CUDA graph, or that runs
+// under a memory pool it may not grow).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+
+#include "../../../include/dmrg_gb300.h"
+#include "../capi_internal.h"
+#include "../exec_errors.h"
+
+namespace {
+
+// Staging for one call: psi in [0, kMaxPsi), sigma in [kMaxPsi, 2 kMaxPsi).
+// 2 x 2^21 doubles = 32 MiB, held by every device that loads the library.
+constexpr int64_t kMaxPsi = int64_t(1) << 21;
+__device__ __align__(256) double g_staging[2 * kMaxPsi];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double* g_addr[kMaxDevices] = {};
+
+dmrg_status fail(dmrg_status s, const std::string& m) {
+  dmrg_internal_set_error(m.c_str());
+  return s;
+}
+
+}  // namespace
+
+extern "C" dmrg_status dmrg_sigma_host_noalloc(dmrg_handle* h, int32_t bond, const double* psi_host,
+                                               double* sigma_host) {
+  try {
+    dmrg_internal_set_error("");
+    if (!h || !psi_host || !sigma_host) return fail(DMRG_ERR_ARG, "null argument");
+    if (h->eng->bond() != bond)
+      return fail(DMRG_ERR_ARG, "bond not prepared: call dmrg_prepare for this bond first");
+    const int64_t n = h->eng->psi_size();
+    if (n > kMaxPsi)
+      return fail(DMRG_ERR_ARG, "psi_size " + std::to_string(n) + " exceeds the allocation-free limit of " +
+                                    std::to_string(kMaxPsi) + " doubles; use dmrg_sigma_host");
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return fail(DMRG_ERR_CUDA, "cudaGetDevice failed");
+    if (cur != h->device) return fail(DMRG_ERR_ARG, "the handle's device is not the current device");
+    if (cur < 0 || cur >= kMaxDevices) return fail(DMRG_ERR_ARG, "device ordinal out of range");
+    double* base = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      if (!g_addr[cur]) {
+        // once per device, with that device current: device address of the array
+        void* p = nullptr;
+        cudaError_t rc = cudaGetSymbolAddress(&p, g_staging);
+        if (rc != cudaSuccess)
+          return fail(DMRG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(rc));
+        g_addr[cur] = static_cast<double*>(p);
+      }
+      base = g_addr[cur];
+    }
+    dmrg::Exec* ex = h->eng->exec();
+    ex->h2d(base, psi_host, size_t(n) * sizeof(double));
+    h->eng->sigma_precision(base, base + kMaxPsi, h->eng->problem().precision);
+    ex->d2h(sigma_host, base + kMaxPsi, size_t(n) * sizeof(double));
+    return DMRG_OK;
+  } catch (const dmrg::CudaError& e) {
+    return fail(DMRG_ERR_CUDA, e.what());
+  } catch (const dmrg::OomError& e) {
+    return fail(DMRG_ERR_OOM, e.what());
+  } catch (const std::exception& e) {
+    return fail(DMRG_ERR_ARG, e.what());
+  } catch (...) {
+    return fail(DMRG_ERR_STATE, "unknown error");
+  }
+}
