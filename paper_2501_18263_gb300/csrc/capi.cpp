@@ -49,6 +49,13 @@ bool finite(const double* p, size_t n) {
   return true;
 }
 
+// a bounded device-side wait that gave up leaves a nonzero error word
+dmrg_status check_device(dmrg_handle* h) {
+  if (h->eng->problem().precision != 0 && h->eng->exec()->device_error())
+    return fail(DMRG_ERR_TIMEOUT, "a tensor-core pipeline wait gave up; destroy the handle");
+  return DMRG_OK;
+}
+
 dmrg_status ensure_bond(dmrg_handle* h, int bond) {
   if (bond < 0 || bond > h->L - 2) return fail(DMRG_ERR_ARG, "bond out of range");
   if (h->eng->bond() != bond) {
@@ -194,7 +201,7 @@ dmrg_status dmrg_sigma(dmrg_handle* h, int32_t bond, const double* psi, double* 
     if (s != DMRG_OK) return s;
     h->eng->sigma_precision(psi, sig, h->eng->problem().precision);
     h->eng->exec()->sync();
-    return DMRG_OK;
+    return check_device(h);
   });
 }
 
@@ -211,7 +218,7 @@ dmrg_status dmrg_sigma_host(dmrg_handle* h, int32_t bond, const double* psi, dou
     ex->d2h(sig, d + h->eng->psi_size(), bytes);
     ex->sync();
     ex->release(d);
-    return DMRG_OK;
+    return check_device(h);
   });
 }
 
@@ -227,6 +234,7 @@ dmrg_status dmrg_davidson(dmrg_handle* h, int32_t bond, double* psi, double tol,
     h->eng->exec()->sync();
     if (energy) *energy = e;
     if (iterations) *iterations = it;
+    if (check_device(h) != DMRG_OK) return DMRG_ERR_TIMEOUT;
     if (!std::isfinite(e)) return fail(DMRG_ERR_NONFINITE, "non-finite energy");
     if (h->eng->last_rnorm > tol) return fail(DMRG_ERR_NOCONV, "Davidson did not reach the tolerance");
     return DMRG_OK;
@@ -251,6 +259,7 @@ dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedu
     h->eng->exec()->sync();
     if (energies)
       for (int s = 0; s < n_sweeps; ++s) energies[s] = e[s];
+    if (check_device(h) != DMRG_OK) return DMRG_ERR_TIMEOUT;
     for (double x : e)
       if (!std::isfinite(x)) return fail(DMRG_ERR_NONFINITE, "non-finite energy");
     return DMRG_OK;

@@ -65,6 +65,7 @@ struct OpBlk {
   int rows, cols;
   int64_t off;       // element offset in the owning arena
   int ident = 0;     // enlarged only: block is c * identity (never read as a matrix)
+  int64_t pn = -1, pt = -1;  // split-BF16 plane offsets: normal and transposed copies
 };
 
 struct Op {
@@ -199,6 +200,22 @@ class Engine {
   double* diag_l_ = nullptr;
   double* diag_r_ = nullptr;
   double* diag_ = nullptr;
+  // split-BF16 tensor-core sigma
+  bool mixed_ready_ = false;
+  uint16_t* oplL_ = nullptr;
+  uint16_t* oplR_ = nullptr;
+  int64_t opsL_ = 0, opsR_ = 0;
+  uint16_t* psiT_ = nullptr;
+  uint16_t* psiN_ = nullptr;
+  int64_t psT_ps_ = 0, psN_ps_ = 0;
+  uint16_t* xpl_ = nullptr;
+  int64_t xpl_ps_ = 0;
+  float* shi_ = nullptr;
+  float* slo_ = nullptr;
+  int psi_split_ = -1;
+  std::vector<Chunk> mchunks_;
+  int mplan_hl_ = -1;
+  void free_mixed();
   // sweep state
   double* psi_cur_ = nullptr;
   int64_t psi_cur_cap_ = 0;

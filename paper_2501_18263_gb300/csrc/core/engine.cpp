@@ -180,7 +180,14 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
   ex_->mdot(V, n, 1, W, n, 1, n, Hs, lds);
   double rnorm = 1e300, th = 0.0;
   int it = 0;
-  bool refined_done = (prec == 0 || !refine);
+  // Mixed precision: iterate with the split-BF16 sigma; when its residual reaches
+  // the level that precision can resolve (or stalls), restart from the Ritz vector
+  // with an FP64 sigma of it.  Corrections added afterwards carry only the small
+  // error of their own (small) coefficients, so the residual is then trusted.
+  const bool mixed = (prec != 0 && refine);
+  int refines = 0, last_refine = -100;
+  double best = 1e300;
+  int best_it = 0;
   for (;; ++it) {
     ex_->ritz(Hs, lds, m, theta, y);
     if (it > 0) {
@@ -197,20 +204,33 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
     ex_->d2h(h2, sc, 2 * sizeof(double));
     th = h2[0];
     rnorm = std::sqrt(std::max(0.0, h2[1]));
-    bool conv = rnorm <= tol;
-    if (conv && !refined_done) {
-      // residual refinement: recompute sigma(x) in FP64 and restart from it
-      refined_done = true;
-      ex_->mdot(x, n, 1, x, n, 1, n, nrm2, 1);
-      ex_->d2d(V, x, n * sizeof(double));
-      ex_->normalize(V, n, nrm2);
-      apply(V, W, 0);
-      ex_->zero(Hs, size_t(lds) * lds * sizeof(double));
-      ex_->mdot(V, n, 1, W, n, 1, n, Hs, lds);
-      m = 1;
-      continue;
+    if (rnorm < 0.9 * best) {
+      best = rnorm;
+      best_it = it;
     }
-    if (conv || it >= max_iter) break;
+    if (!mixed) {
+      if (rnorm <= tol) break;
+    } else {
+      if (refines > 0 && rnorm <= tol) break;
+      const double floor_m = 1e-6 * std::max(1.0, std::fabs(th));
+      const bool stalled = it - best_it >= 8;
+      if ((rnorm <= std::max(tol, floor_m) || stalled) && it - last_refine >= 4 && refines < 8) {
+        ++refines;
+        last_refine = it;
+        best = 1e300;
+        best_it = it;
+        ex_->mdot(x, n, 1, x, n, 1, n, nrm2, 1);
+        ex_->d2d(V, x, n * sizeof(double));
+        ex_->normalize(V, n, nrm2);
+        apply(V, W, 0);
+        ex_->zero(Hs, size_t(lds) * lds * sizeof(double));
+        ex_->mdot(V, n, 1, W, n, 1, n, Hs, lds);
+        m = 1;
+        have_prev = false;
+        continue;
+      }
+    }
+    if (it >= max_iter) break;
     if (m == max_sub) {
       // restart with the current Ritz vector and the part of the previous one
       // orthogonal to it (two-vector restart)

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
+#include <tuple>
 
 #include "core.h"
 
@@ -60,9 +61,31 @@ void Engine::free_bond() {
     if (*p) ex_->release(*p);
     *p = nullptr;
   }
+  free_mixed();
   free_opset(EopsL_);
   free_opset(EopsR_);
   bond_ = -1;
+}
+
+void Engine::free_mixed() {
+  for (auto& c : mchunks_) {
+    if (c.plan1 >= 0) ex_->mix_plan_free(c.plan1);
+    if (c.plan2 >= 0) ex_->mix_plan_free(c.plan2);
+  }
+  mchunks_.clear();
+  if (mplan_hl_ >= 0) ex_->mix_plan_free(mplan_hl_);
+  mplan_hl_ = -1;
+  if (psi_split_ >= 0) ex_->split_plan_free(psi_split_);
+  psi_split_ = -1;
+  for (uint16_t** p : {&oplL_, &oplR_, &psiT_, &psiN_, &xpl_}) {
+    if (*p) ex_->release(*p);
+    *p = nullptr;
+  }
+  for (float** p : {&shi_, &slo_}) {
+    if (*p) ex_->release(*p);
+    *p = nullptr;
+  }
+  mixed_ready_ = false;
 }
 
 void Engine::prepare_bond(int bond) {
@@ -358,6 +381,232 @@ void Engine::build_sigma_plan() {
     st_.n_gemm_problems += int(P3.size());
     st_.n_gemm_segments += int(S3.size());
   }
+  // ---- split-BF16 tensor-core plans (precision 1): same terms and chunks as
+  // above, evaluated on coarse (sector-level) blocks so that each stage is one
+  // GEMM per block pair: stage 1 X{iT, jR} = O_L{iT <- iL} psi{iL, jR} with K =
+  // the padded rows of iL, stage 2 sigma{iT, jT} = sum_nu X_nu{iT, jR} O_R{jT <- jR}^T
+  // with K concatenated over all terms.  Fine sub-blocks that are zero stay zero
+  // in the coarse planes.
+  if (P_.precision != 0) {
+    auto pad8 = [](int64_t x) { return (x + 7) & ~int64_t(7); };
+    std::vector<int> rowpad(EL.coarse.q.size(), 0), colpad(ER.coarse.q.size(), 0);
+    std::vector<int> rp(EL.f_dim.size(), 0), cp(ER.f_dim.size(), 0);
+    for (size_t i = 0; i < EL.coarse.q.size(); ++i)
+      for (int f : EL.coarse_fines[i]) {
+        rp[f] = rowpad[i];
+        rowpad[i] += int(pad8(EL.f_dim[f]));
+      }
+    for (size_t j = 0; j < ER.coarse.q.size(); ++j)
+      for (int g : ER.coarse_fines[j]) {
+        cp[g] = colpad[j];
+        colpad[j] += int(pad8(ER.f_dim[g]));
+      }
+    // coarse operator planes: normal N(a <- b) is dim(a) x pad(b); transposed
+    // T(a <- b) holds (O^T){b <- a} as dim(b) x pad(a)
+    using CKey = std::tuple<const Op*, int, int>;
+    std::map<CKey, std::pair<int64_t, int64_t>> offL, offR;
+    auto planes = [&](const OpSet& os, const Enlarged& E, const std::vector<int>& pad, const std::vector<int>& pp,
+                      std::map<CKey, std::pair<int64_t, int64_t>>& off, uint16_t*& arena, int64_t& ps) {
+      int64_t o = 0;
+      for (auto& kv : os.ops)
+        for (auto& bk : kv.second.blk) {
+          const int ca = E.f_coarse[bk.r], cb = E.f_coarse[bk.c];
+          CKey key{&kv.second, ca, cb};
+          if (off.count(key)) continue;
+          const int64_t on = o;
+          o += int64_t(E.coarse.dim[ca]) * pad[cb];
+          const int64_t ot = o;
+          o += int64_t(E.coarse.dim[cb]) * pad[ca];
+          off[key] = {on, ot};
+        }
+      ps = pad8(o) + 8;
+      arena = static_cast<uint16_t*>(ex_->alloc(size_t(3 * ps) * sizeof(uint16_t)));
+      ex_->zero(arena, size_t(3 * ps) * sizeof(uint16_t));
+      std::vector<SplitTask> tk;
+      for (auto& kv : os.ops)
+        for (auto& bk : kv.second.blk) {
+          const int ca = E.f_coarse[bk.r], cb = E.f_coarse[bk.c];
+          const auto& oo = off[CKey{&kv.second, ca, cb}];
+          tk.push_back(SplitTask{os.arena + bk.off, bk.rows, bk.cols, bk.cols, pad[cb], pad[ca], 0,
+                                 arena + oo.first + int64_t(E.f_row[bk.r]) * pad[cb] + pp[bk.c],
+                                 arena + oo.second + int64_t(E.f_row[bk.c]) * pad[ca] + pp[bk.r], ps});
+        }
+      int sp = ex_->split_plan(tk);
+      ex_->split_run(sp);
+      ex_->split_plan_free(sp);
+    };
+    planes(EopsL_, EL, rowpad, rp, offL, oplL_, opsL_);
+    planes(EopsR_, ER, colpad, cp, offR, oplR_, opsR_);
+    // psi planes: psiN (rows x colpad), psiT (colpad x rowpad), psiTu (cols x rowpad)
+    std::vector<int64_t> tOff(EL.coarse.q.size(), -1), nOff(EL.coarse.q.size(), -1), uOff(EL.coarse.q.size(), -1);
+    int64_t tT = 0, tN = 0, tU = 0;
+    for (size_t i = 0; i < EL.coarse.q.size(); ++i) {
+      if (psi_off_[i] < 0) continue;
+      const int j = psi_rcoarse_[i];
+      tOff[i] = tT;
+      tT += int64_t(colpad[j]) * rowpad[i];
+      nOff[i] = tN;
+      tN += int64_t(EL.coarse.dim[i]) * colpad[j];
+      uOff[i] = tU;
+      tU += int64_t(ER.coarse.dim[j]) * rowpad[i];
+    }
+    psT_ps_ = pad8(tT) + 8;
+    psN_ps_ = pad8(tN) + 8;
+    const int64_t psU_ps = pad8(tU) + 8;
+    psiT_ = static_cast<uint16_t*>(ex_->alloc(size_t(3 * psT_ps_) * sizeof(uint16_t)));
+    psiN_ = static_cast<uint16_t*>(ex_->alloc(size_t(3 * (psN_ps_ + psU_ps)) * sizeof(uint16_t)));
+    uint16_t* psiU = psiN_ + 3 * psN_ps_;
+    ex_->zero(psiT_, size_t(3 * psT_ps_) * sizeof(uint16_t));
+    ex_->zero(psiN_, size_t(3 * (psN_ps_ + psU_ps)) * sizeof(uint16_t));
+    {
+      std::vector<SplitTask> tk;
+      for (size_t i = 0; i < EL.coarse.q.size(); ++i) {
+        if (psi_off_[i] < 0) continue;
+        const int j = psi_rcoarse_[i];
+        const int cols = ER.coarse.dim[j];
+        for (int f : EL.coarse_fines[i])
+          for (int g : ER.coarse_fines[j]) {
+            const double* src = psi_in_ + psi_off_[i] + int64_t(EL.f_row[f]) * cols + ER.f_row[g];
+            tk.push_back(SplitTask{src, EL.f_dim[f], ER.f_dim[g], cols, colpad[j], rowpad[i], 0,
+                                   psiN_ + nOff[i] + int64_t(EL.f_row[f]) * colpad[j] + cp[g], nullptr, psN_ps_});
+            tk.push_back(SplitTask{src, EL.f_dim[f], ER.f_dim[g], cols, colpad[j], rowpad[i], 0, nullptr,
+                                   psiT_ + tOff[i] + int64_t(cp[g]) * rowpad[i] + rp[f], psT_ps_});
+            tk.push_back(SplitTask{src, EL.f_dim[f], ER.f_dim[g], cols, colpad[j], rowpad[i], 0, nullptr,
+                                   psiU + uOff[i] + int64_t(ER.f_row[g]) * rowpad[i] + rp[f], psU_ps});
+          }
+      }
+      psi_split_ = ex_->split_plan(tk);
+    }
+    // X planes per chunk: X{iT, jR} is rows(iT) x colpad(jR)
+    std::vector<std::vector<int64_t>> xmoff(T.size());
+    std::vector<int64_t> xmsize(T.size(), 0);
+    for (size_t n = 0; n < T.size(); ++n) {
+      int64_t o = 0;
+      for (const XBlk& xb : xl[n]) {
+        xmoff[n].push_back(o);
+        o += int64_t(EL.coarse.dim[xb.iT]) * colpad[xb.jR];
+      }
+      xmsize[n] = o;
+    }
+    int64_t xmax_m = 0;
+    for (auto& rg : ranges) {
+      int64_t a = 0;
+      for (size_t n = rg.first; n < rg.second; ++n) a += xmsize[n];
+      xmax_m = std::max(xmax_m, a);
+    }
+    xpl_ps_ = pad8(xmax_m) + 8;
+    xpl_ = static_cast<uint16_t*>(ex_->alloc(size_t(3 * xpl_ps_) * sizeof(uint16_t)));
+    shi_ = static_cast<float*>(ex_->alloc(psi_n_ * sizeof(float)));
+    slo_ = static_cast<float*>(ex_->alloc(psi_n_ * sizeof(float)));
+    for (size_t ci = 0; ci < ranges.size(); ++ci) {
+      const size_t n0 = ranges[ci].first, n1 = ranges[ci].second;
+      std::vector<int64_t> xb0(T.size(), 0);
+      {
+        int64_t a = 0;
+        for (size_t n = n0; n < n1; ++n) {
+          xb0[n] = a;
+          a += xmsize[n];
+        }
+      }
+      std::vector<MixProb> P1;
+      std::vector<MixSeg> S1;
+      for (size_t n = n0; n < n1; ++n) {
+        const Term& t = T[n];
+        if (!t.L) continue;
+        for (size_t k = 0; k < xl[n].size(); ++k) {
+          const XBlk& xb = xl[n][k];
+          const QN qL = EL.coarse.q[xb.iL];
+          const double sg = (t.R && t.R->odd && (qL.n() & 1)) ? -1.0 : 1.0;
+          MixProb q{};
+          q.Cp = xpl_ + xb0[n] + xmoff[n][k];
+          q.psC = xpl_ps_;
+          q.ldc = colpad[xb.jR];
+          q.M = EL.coarse.dim[xb.iT];
+          q.N = colpad[xb.jR];
+          q.alpha = float(t.c * sg);
+          q.mode = 1;
+          q.accumulate = 0;
+          q.s0 = int(S1.size());
+          const CKey key = t.Lt ? CKey{t.L, xb.iL, xb.iT} : CKey{t.L, xb.iT, xb.iL};
+          auto it = offL.find(key);
+          if (it != offL.end()) {
+            const int64_t o = t.Lt ? it->second.second : it->second.first;
+            S1.push_back(MixSeg{oplL_ + o, psiT_ + tOff[xb.iL], opsL_, psT_ps_, rowpad[xb.iL], rowpad[xb.iL],
+                                rowpad[xb.iL], 0});
+          }
+          q.s1 = int(S1.size());
+          P1.push_back(q);
+        }
+      }
+      std::vector<MixProb> P2;
+      std::vector<MixSeg> S2;
+      for (size_t iT = 0; iT < EL.coarse.q.size(); ++iT) {
+        if (psi_off_[iT] < 0) continue;
+        const int jT = psi_rcoarse_[iT];
+        MixProb q{};
+        q.Chi = shi_ + psi_off_[iT];
+        q.Clo = slo_ + psi_off_[iT];
+        q.ldc = ER.coarse.dim[jT];
+        q.M = EL.coarse.dim[iT];
+        q.N = ER.coarse.dim[jT];
+        q.alpha = 1.0f;
+        q.mode = 0;
+        q.accumulate = ci > 0;
+        q.s0 = int(S2.size());
+        for (size_t n = n0; n < n1; ++n) {
+          const Term& t = T[n];
+          QN dR = t.Rt ? QN{0, 0} - t.R->delta : t.R->delta;
+          const int jR = rcoarse(ER.coarse.q[jT] - dR);
+          if (jR < 0) continue;
+          const CKey key = t.Rt ? CKey{t.R, jR, jT} : CKey{t.R, jT, jR};
+          auto it = offR.find(key);
+          if (it == offR.end()) continue;
+          const uint16_t* B = oplR_ + (t.Rt ? it->second.second : it->second.first);
+          if (!t.L) {
+            if (jR != jT) continue;
+            S2.push_back(MixSeg{psiN_ + nOff[iT], B, psN_ps_, opsR_, colpad[jT], colpad[jT], colpad[jT], 0});
+          } else {
+            const int xi = xidx[n][iT];
+            if (xi < 0 || xl[n][xi].jR != jR) continue;
+            S2.push_back(MixSeg{xpl_ + xb0[n] + xmoff[n][xi], B, xpl_ps_, opsR_, colpad[jR], colpad[jR], colpad[jR], 0});
+          }
+        }
+        q.s1 = int(S2.size());
+        P2.push_back(q);
+      }
+      Chunk ch;
+      ch.plan1 = P1.empty() ? -1 : ex_->mix_plan(P1, S1);
+      ch.plan2 = ex_->mix_plan(P2, S2);
+      mchunks_.push_back(ch);
+    }
+    {
+      const Op* HL = GL(OP_H, 0);
+      std::vector<MixProb> P3;
+      std::vector<MixSeg> S3;
+      for (size_t i = 0; i < EL.coarse.q.size(); ++i) {
+        if (psi_off_[i] < 0) continue;
+        const int j = psi_rcoarse_[i];
+        auto it = offL.find(CKey{HL, int(i), int(i)});
+        if (it == offL.end()) continue;
+        MixProb q{};
+        q.Chi = shi_ + psi_off_[i];
+        q.Clo = slo_ + psi_off_[i];
+        q.ldc = ER.coarse.dim[j];
+        q.M = EL.coarse.dim[i];
+        q.N = ER.coarse.dim[j];
+        q.alpha = 1.0f;
+        q.mode = 0;
+        q.accumulate = 1;
+        q.s0 = int(S3.size());
+        S3.push_back(MixSeg{oplL_ + it->second.first, psiU + uOff[i], opsL_, psU_ps, rowpad[i], rowpad[i], rowpad[i], 0});
+        q.s1 = int(S3.size());
+        P3.push_back(q);
+      }
+      mplan_hl_ = P3.empty() ? -1 : ex_->mix_plan(P3, S3);
+    }
+    mixed_ready_ = true;
+  }
+
   // algorithmic operator bytes (each used operator block read once)
   {
     int64_t e = 0;
@@ -449,8 +698,18 @@ void Engine::sigma(const double* psi, double* sig) {
 }
 
 void Engine::sigma_precision(const double* psi, double* sig, int precision) {
-  (void)precision;
-  sigma(psi, sig);
+  if (precision == 0 || !mixed_ready_) {
+    sigma(psi, sig);
+    return;
+  }
+  ex_->d2d(psi_in_, psi, psi_n_ * sizeof(double));
+  ex_->split_run(psi_split_);
+  for (auto& c : mchunks_) {
+    if (c.plan1 >= 0) ex_->mix_run(c.plan1);
+    ex_->mix_run(c.plan2);
+  }
+  if (mplan_hl_ >= 0) ex_->mix_run(mplan_hl_);
+  ex_->df_to_f64(shi_, slo_, sig, psi_n_);
 }
 
 void Engine::rdm(const double* lam, const double* psi, double* g1, double* g2) {

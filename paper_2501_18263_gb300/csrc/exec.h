@@ -47,6 +47,39 @@ struct DiagTask {
   double coef;
 };
 
+// ---- split-BF16 tensor-core path -------------------------------------------
+// Operands are stored as three BF16 planes (x ~ hi + mid + lo), plane p of an
+// operand at ptr + p * plane_stride.  Every operand is K-major: row r holds K
+// contiguous elements at ptr + r * ld; rows start on 16-byte boundaries (ld and
+// plane strides multiples of 8 elements) and the elements between K and
+// round8(K) are zero.
+struct MixSeg {
+  const uint16_t* A;   // M rows (tile rows) x K
+  const uint16_t* B;   // N rows (tile cols) x K
+  int64_t psA, psB;
+  int lda, ldb, K, pad;
+};
+// C (M x N) = alpha * sum_seg A_seg B_seg^T
+//   mode 0: C kept as a float pair (hi, lo) at Chi/Clo (+= if accumulate)
+//   mode 1: C written as three BF16 planes at Cp (plane stride psC)
+struct MixProb {
+  float* Chi;
+  float* Clo;
+  uint16_t* Cp;
+  int64_t psC;
+  int ldc, M, N, s0, s1;
+  float alpha;
+  int mode, accumulate;
+};
+// FP64 block (rows x cols, ld) -> BF16 planes, normal (rows x ldn) and/or transposed (cols x ldt)
+struct SplitTask {
+  const double* src;
+  int rows, cols, ld, ldn, ldt, pad;
+  uint16_t* dn;
+  uint16_t* dt;
+  int64_t ps;
+};
+
 class Exec {
  public:
   virtual ~Exec() {}
@@ -89,6 +122,17 @@ class Exec {
   // (ld = n_b, destroyed), w_b ascending eigenvalues, Z_b eigenvectors as columns (ld n_b)
   virtual void syev(const std::vector<double*>& A, const std::vector<double*>& w,
                     const std::vector<double*>& Z, const std::vector<int>& n) = 0;
+
+  // split-BF16 tensor-core GEMM plans (tcgen05 / TMEM)
+  virtual int mix_plan(const std::vector<MixProb>& p, const std::vector<MixSeg>& s) = 0;
+  virtual void mix_run(int plan) = 0;
+  virtual void mix_plan_free(int plan) = 0;
+  virtual int split_plan(const std::vector<SplitTask>& t) = 0;
+  virtual void split_run(int plan) = 0;
+  virtual void split_plan_free(int plan) = 0;
+  virtual void df_to_f64(const float* hi, const float* lo, double* out, int64_t n) = 0;
+  // nonzero when a bounded device-side wait gave up (read with a stream sync)
+  virtual int device_error() = 0;
 
   // kernel timing with events on the stream: mode 1 resets and starts, mode 0 stops
   // and fills out[2*c] = milliseconds, out[2*c+1] = launches for each kernel class c

@@ -15,6 +15,7 @@
 
 #include "../exec.h"
 #include "../exec_errors.h"
+#include "mixed.h"
 
 namespace dmrg {
 
@@ -460,13 +461,20 @@ class CudaExec : public Exec {
     CK(cudaGetDevice(&dev_));
     CK(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev_));
     CK(cudaMalloc(&part_, sizeof(double) * 1024 * MDOT_MAX * 4));
+    CK(cudaMalloc(&err_, sizeof(int)));
+    CK(cudaMemsetAsync(err_, 0, sizeof(int), st_));
   }
   ~CudaExec() override {
     try { drain(); } catch (...) {}
     for (auto& m : marks_) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : pool_) cudaEventDestroy(e);
     for (auto& p : plans_) free_plan_mem(p);
+    for (size_t i = 0; i < mplans_.size(); ++i) mix_free(int(i));
+    for (auto& p : splans_)
+      if (p.live) cudaFreeAsync(p.t, st_);
+    cudaStreamSynchronize(st_);
     cudaFree(part_);
+    cudaFree(err_);
   }
   void* alloc(size_t b) override {
     void* p = nullptr;
@@ -572,6 +580,95 @@ class CudaExec : public Exec {
     DiagTask* d = upload(t);
     launch(PROF_VEC, [&] { diag_kernel<<<std::min<size_t>(t.size(), 65535), 128, 0, st_>>>(d, int(t.size())); });
     release(d);
+  }
+
+  // ---- split-BF16 tensor-core path
+  struct MixPlanD {
+    MixTile* tiles = nullptr;
+    MixProb* probs = nullptr;
+    MixSeg* segs = nullptr;
+    int ntiles = 0;
+    bool live = false;
+  };
+  struct SplitPlanD {
+    SplitTask* t = nullptr;
+    int n = 0;
+    bool live = false;
+  };
+  std::vector<MixPlanD> mplans_;
+  std::vector<SplitPlanD> splans_;
+  int* err_ = nullptr;
+
+  int mix_plan(const std::vector<MixProb>& p, const std::vector<MixSeg>& s) override {
+    for (const MixSeg& g : s) {
+      if ((reinterpret_cast<uintptr_t>(g.A) & 15) || (reinterpret_cast<uintptr_t>(g.B) & 15) || (g.lda & 7) ||
+          (g.ldb & 7) || (g.psA & 7) || (g.psB & 7) || g.K <= 0)
+        throw std::runtime_error("mix_plan: operand not 16-byte aligned / padded");
+    }
+    std::vector<MixTile> tiles;
+    for (size_t i = 0; i < p.size(); ++i)
+      for (int m0 = 0; m0 < p[i].M; m0 += MIX_TM)
+        for (int n0 = 0; n0 < p[i].N; n0 += MIX_TN) tiles.push_back(MixTile{int(i), m0, n0, 0});
+    MixPlanD pl;
+    pl.ntiles = int(tiles.size());
+    pl.tiles = upload(tiles);
+    pl.probs = upload(p);
+    pl.segs = upload(s);
+    pl.live = true;
+    for (size_t i = 0; i < mplans_.size(); ++i)
+      if (!mplans_[i].live) {
+        mplans_[i] = pl;
+        return int(i);
+      }
+    mplans_.push_back(pl);
+    return int(mplans_.size() - 1);
+  }
+  void mix_run(int id) override {
+    MixPlanD& pl = mplans_.at(id);
+    if (!pl.ntiles) return;
+    launch(PROF_MIXED, [&] { launch_mixed_gemm(pl.tiles, pl.ntiles, pl.probs, pl.segs, err_, st_); });
+  }
+  void mix_plan_free(int id) override { mix_free(id); }
+  void split_plan_free(int id) override {
+    SplitPlanD& pl = splans_.at(id);
+    if (!pl.live) return;
+    cudaFreeAsync(pl.t, st_);
+    pl.live = false;
+  }
+  void mix_free(int id) {
+    MixPlanD& pl = mplans_.at(id);
+    if (!pl.live) return;
+    cudaFreeAsync(pl.tiles, st_);
+    cudaFreeAsync(pl.probs, st_);
+    cudaFreeAsync(pl.segs, st_);
+    pl.live = false;
+  }
+  int split_plan(const std::vector<SplitTask>& t) override {
+    SplitPlanD pl;
+    pl.n = int(t.size());
+    pl.t = upload(t);
+    pl.live = true;
+    for (size_t i = 0; i < splans_.size(); ++i)
+      if (!splans_[i].live) {
+        splans_[i] = pl;
+        return int(i);
+      }
+    splans_.push_back(pl);
+    return int(splans_.size() - 1);
+  }
+  void split_run(int id) override {
+    SplitPlanD& pl = splans_.at(id);
+    if (!pl.n) return;
+    launch(PROF_SPLIT, [&] { launch_split(pl.t, pl.n, st_); });
+  }
+  void df_to_f64(const float* hi, const float* lo, double* out, int64_t n) override {
+    launch(PROF_SPLIT, [&] { launch_df_to_f64(hi, lo, out, n, grid_for(n), st_); });
+  }
+  int device_error() override {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, err_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
+    return h;
   }
 
   int grid_for(int64_t n) const { return int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, int64_t(nsm_) * 8))); }

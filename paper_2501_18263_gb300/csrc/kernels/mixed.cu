@@ -1,0 +1,446 @@
+// Split-BF16 grouped GEMM on the 5th-generation tensor cores (tcgen05 + TMEM).
+//
+// Each operand x is carried as three BF16 planes with x ~ hi + mid + lo
+// (residual below 2^-27 |x|).  A tile computes
+//     acc0 = sum hi_A hi_B                                   (TMEM columns [0, 128))
+//     acc1 = sum hi mid + mid hi + hi lo + mid mid + lo hi   (TMEM columns [128, 256))
+// so that the rounding of the five small products happens in an accumulator
+// 2^8 smaller than the result.  Every product of two BF16 values is exact in
+// FP32, but the tensor core's FP32 accumulation loses about a third of an ulp
+// per K = 16 step, so the accumulators only ever hold one chunk of K (CHUNK
+// stages): after each chunk they are drained into a double-float running sum
+// (hi + lo, TwoSum) kept in TMEM columns [256, 512).
+//
+// CTA = 9 warps.  Warp 0 allocates TMEM and one elected lane issues the MMAs;
+// warps 1-4 load operand tiles (16-byte vector loads into the canonical
+// no-swizzle K-major core-matrix layout); warps 5-8 drain the accumulators and
+// run the epilogue.  A ring of four shared-memory stages is guarded by
+// mbarriers; every wait is bounded and sets an error word instead of hanging.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mixed.h"
+
+namespace dmrg {
+namespace {
+
+constexpr int BK = 32;                          // K elements per stage
+constexpr int STAGES = 4;
+constexpr int PLANE_BYTES = MIX_TM * BK * 2;    // one 128 x 32 BF16 plane: 8 KiB
+constexpr int STAGE_BYTES = 6 * PLANE_BYTES;    // 3 A planes + 3 B planes
+constexpr int BAR_BYTES = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES;
+constexpr int NTHREADS = 288;
+constexpr int CHUNK = 4;                        // K stages per accumulator drain (128 K)
+constexpr long long WAIT_CYCLES = 4000000000LL; // about 2 s at 2 GHz
+constexpr uint32_t TMEM_COLS = 512;
+
+static_assert(MIX_TN == MIX_TM, "B tile uses the A plane size");
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: gives up after WAIT_CYCLES or when another role aborted
+__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* err, int code) {
+  const long long t0 = clock64();
+  while (!mbar_try(a, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      *abort_flag = 1;
+      atomicExch(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+// shared-memory matrix descriptor: canonical K-major layout without swizzle,
+// core matrices of 8 rows x 16 bytes; LBO = 128 B (next core matrix along K),
+// SBO = 512 B (next 8-row group along M/N, BK/8 core matrices per group)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>((128u >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>(((BK / 8) * 128u >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;  // descriptor version of the 5th-generation tensor core
+  return d;
+}
+
+// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both operands K-major
+__device__ __forceinline__ uint32_t idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(MIX_TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// two 32-lane x 16-column loads (acc0 and acc1 chunks) and the wait, in one statement
+__device__ __forceinline__ void tmem_ld2(uint32_t t0, uint32_t t1, float* v0, float* v1) {
+  uint32_t a[16], b[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+        "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]),
+        "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]),
+        "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15])
+      : "r"(t0), "r"(t1)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    v0[i] = __uint_as_float(a[i]);
+    v1[i] = __uint_as_float(b[i]);
+  }
+}
+
+__device__ __forceinline__ void tmem_st2(uint32_t t0, uint32_t t1, const float* v0, const float* v1) {
+  uint32_t a[16], b[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    a[i] = __float_as_uint(v0[i]);
+    b[i] = __float_as_uint(v1[i]);
+  }
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%32], {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15};\n\t"
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%33], {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31};\n\t"
+      "tcgen05.wait::st.sync.aligned;\n" ::"r"(a[0]),
+      "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[8]), "r"(a[9]),
+      "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), "r"(a[15]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
+      "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]),
+      "r"(b[12]), "r"(b[13]), "r"(b[14]), "r"(b[15]), "r"(t0), "r"(t1)
+      : "memory");
+}
+
+__device__ __forceinline__ uint16_t bf_bits(__nv_bfloat16 x) { return __bfloat16_as_ushort(x); }
+
+// error-free sum of two floats (TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    mixed_gemm_kernel(const MixTile* __restrict__ tiles, const MixProb* __restrict__ probs,
+                      const MixSeg* __restrict__ segs, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars: full[STAGES], empty[STAGES], chunk_done, drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const MixTile tl = tiles[blockIdx.x];
+  const MixProb p = probs[tl.prob];
+  const int Nt = min(MIX_TN, p.N - tl.n0);
+  const int Nmma = (Nt + 15) & ~15;
+  int nsteps = 0;
+  for (int s = p.s0; s < p.s1; ++s) nsteps += (segs[s].K + BK - 1) / BK;
+  const int nchunks = (nsteps + CHUNK - 1) / CHUNK;
+
+  auto full = [&](int s) { return saddr(&bars[s]); };
+  auto empty = [&](int s) { return saddr(&bars[STAGES + s]); };
+  const uint32_t chunk_done = saddr(&bars[2 * STAGES]);
+  const uint32_t drained = saddr(&bars[2 * STAGES + 1]);
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 128);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(chunk_done, 1);
+    mbar_init(drained, 128);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---- MMA issuer
+    if (lane == 0 && nsteps > 0) {
+      const uint32_t id = idesc(Nmma);
+      int step = 0, in_chunk = 0, chunk = 0;
+      for (int s = p.s0; s < p.s1; ++s) {
+        const int K = segs[s].K;
+        for (int k0 = 0; k0 < K; k0 += BK, ++step) {
+          const int st = step % STAGES;
+          if (in_chunk == 0 && chunk > 0 &&
+              !mbar_wait(drained, (chunk - 1) & 1, abort_flag, err, 4))
+            goto mma_done;
+          if (!mbar_wait(full(st), (step / STAGES) & 1, abort_flag, err, 1)) goto mma_done;
+          fence_after();
+          const uint32_t base = saddr(smem + st * STAGE_BYTES);
+          const int ksub = (K - k0 > 16) ? 2 : 1;
+          for (int kk = 0; kk < ksub; ++kk) {
+            const uint32_t o = kk * 256;
+            const uint64_t a0 = sdesc(base + o), a1 = sdesc(base + PLANE_BYTES + o),
+                           a2 = sdesc(base + 2 * PLANE_BYTES + o);
+            const uint64_t b0 = sdesc(base + 3 * PLANE_BYTES + o), b1 = sdesc(base + 4 * PLANE_BYTES + o),
+                           b2 = sdesc(base + 5 * PLANE_BYTES + o);
+            const uint32_t acc = (in_chunk == 0 && kk == 0) ? 0u : 1u;
+            mma(tmem, a0, b0, id, acc);
+            mma(tmem + 128, a0, b1, id, acc);
+            mma(tmem + 128, a1, b0, id, 1u);
+            mma(tmem + 128, a0, b2, id, 1u);
+            mma(tmem + 128, a1, b1, id, 1u);
+            mma(tmem + 128, a2, b0, id, 1u);
+          }
+          mma_commit(empty(st));
+          if (++in_chunk == CHUNK) {
+            mma_commit(chunk_done);
+            in_chunk = 0;
+            ++chunk;
+          }
+        }
+      }
+      if (in_chunk > 0) mma_commit(chunk_done);
+      goto mma_end;
+    mma_done:
+      // aborted: release the drain warps waiting for the current chunk
+      mma_commit(chunk_done);
+    mma_end:;
+    }
+    __syncwarp();
+  } else if (warp <= 4) {
+    // ---- producers: warps 1..4
+    const int pt = tid - 32;
+    int step = 0;
+    bool stop = false;
+    for (int s = p.s0; s < p.s1 && !stop; ++s) {
+      const MixSeg g = segs[s];
+      const int Kp = (g.K + 7) & ~7;
+      for (int k0 = 0; k0 < g.K; k0 += BK, ++step) {
+        const int st = step % STAGES;
+        if (step >= STAGES && !mbar_wait(empty(st), ((step / STAGES) - 1) & 1, abort_flag, err, 2)) {
+          stop = true;
+          break;
+        }
+        uint8_t* base = smem + st * STAGE_BYTES;
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+          const int idx = pt + it * 128;
+          const int r = idx >> 2, j = idx & 3;
+          const int k = k0 + 8 * j;
+          const uint32_t so = (((r >> 3) * (BK / 8) + j) << 7) + ((r & 7) << 4);
+          uint4 va[3], vb[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) va[q] = vb[q] = make_uint4(0, 0, 0, 0);
+          const int gm = tl.m0 + r, gn = tl.n0 + r;
+          if (gm < p.M && k < Kp) {
+            const uint16_t* a = g.A + int64_t(gm) * g.lda + k;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) va[q] = __ldg(reinterpret_cast<const uint4*>(a + q * g.psA));
+          }
+          if (r < Nmma && gn < p.N && k < Kp) {
+            const uint16_t* b = g.B + int64_t(gn) * g.ldb + k;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) vb[q] = __ldg(reinterpret_cast<const uint4*>(b + q * g.psB));
+          }
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            *reinterpret_cast<uint4*>(base + q * PLANE_BYTES + so) = va[q];
+            *reinterpret_cast<uint4*>(base + (3 + q) * PLANE_BYTES + so) = vb[q];
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(full(st));
+      }
+    }
+  } else {
+    // ---- drain + epilogue: warps 5..8, TMEM lane quarter warp % 4
+    const int q4 = warp & 3;
+    const int row = q4 * 32 + lane;
+    const int gm = tl.m0 + row;
+    const uint32_t lb = tmem + (static_cast<uint32_t>(q4 * 32) << 16);
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      if (ok) ok = mbar_wait(chunk_done, c & 1, abort_flag, err, 3);
+      ok = __all_sync(0xffffffffu, ok);
+      fence_after();
+      const bool last = (c == nchunks - 1);
+      for (int c0 = 0; c0 < Nmma; c0 += 16) {
+        float v0[16], v1[16], sh[16], sl[16];
+        if (ok) {
+          tmem_ld2(lb + c0, lb + 128 + c0, v0, v1);
+          if (c > 0) tmem_ld2(lb + 256 + c0, lb + 384 + c0, sh, sl);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v0[i] = v1[i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float hi, lo;
+          two_sum(v0[i], v1[i], hi, lo);
+          if (c > 0 && ok) {
+            float s, e;
+            two_sum(sh[i], hi, s, e);
+            e += sl[i] + lo;
+            hi = s + e;
+            lo = e - (hi - s);
+          }
+          sh[i] = hi;
+          sl[i] = lo;
+        }
+        if (!last) {
+          if (ok) tmem_st2(lb + 256 + c0, lb + 384 + c0, sh, sl);
+          continue;
+        }
+        if (gm >= p.M) continue;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (c0 + i >= Nt) break;
+          const int64_t o = int64_t(gm) * p.ldc + tl.n0 + c0 + i;
+          if (p.mode == 0) {
+            float hi = p.alpha * sh[i], lo = p.alpha * sl[i];
+            if (p.accumulate) {
+              float s, e;
+              two_sum(p.Chi[o], hi, s, e);
+              e += p.Clo[o] + lo;
+              hi = s + e;
+              lo = e - (hi - s);
+            }
+            p.Chi[o] = hi;
+            p.Clo[o] = lo;
+          } else {
+            const float a0 = p.alpha * sh[i], a1 = p.alpha * sl[i];
+            const __nv_bfloat16 h = __float2bfloat16_rn(a0);
+            const float r = (a0 - __bfloat162float(h)) + a1;
+            const __nv_bfloat16 m = __float2bfloat16_rn(r);
+            const __nv_bfloat16 l = __float2bfloat16_rn(r - __bfloat162float(m));
+            p.Cp[o] = bf_bits(h);
+            p.Cp[o + p.psC] = bf_bits(m);
+            p.Cp[o + 2 * p.psC] = bf_bits(l);
+          }
+        }
+      }
+      if (!last) {
+        fence_before();
+        mbar_arrive(drained);
+      }
+    }
+    if (nchunks == 0 && gm < p.M) {
+      // no contribution: C = 0 (or unchanged when accumulating)
+      for (int i = 0; i < Nt; ++i) {
+        const int64_t o = int64_t(gm) * p.ldc + tl.n0 + i;
+        if (p.mode == 0) {
+          if (!p.accumulate) {
+            p.Chi[o] = 0.f;
+            p.Clo[o] = 0.f;
+          }
+        } else {
+          p.Cp[o] = 0;
+          p.Cp[o + p.psC] = 0;
+          p.Cp[o + 2 * p.psC] = 0;
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+__global__ void split_kernel(const SplitTask* __restrict__ t, int nt) {
+  for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+    const SplitTask s = t[i];
+    const int n = s.rows * s.cols;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int r = e / s.cols, c = e - r * s.cols;
+      const double x = s.src[int64_t(r) * s.ld + c];
+      const __nv_bfloat16 h = __double2bfloat16(x);
+      const double r1 = x - static_cast<double>(__bfloat162float(h));
+      const __nv_bfloat16 m = __double2bfloat16(r1);
+      const double r2 = r1 - static_cast<double>(__bfloat162float(m));
+      const __nv_bfloat16 l = __double2bfloat16(r2);
+      if (s.dn) {
+        uint16_t* d = s.dn + int64_t(r) * s.ldn + c;
+        d[0] = bf_bits(h);
+        d[s.ps] = bf_bits(m);
+        d[2 * s.ps] = bf_bits(l);
+      }
+      if (s.dt) {
+        uint16_t* d = s.dt + int64_t(c) * s.ldt + r;
+        d[0] = bf_bits(h);
+        d[s.ps] = bf_bits(m);
+        d[2 * s.ps] = bf_bits(l);
+      }
+    }
+  }
+}
+
+__global__ void df_to_f64_kernel(const float* __restrict__ hi, const float* __restrict__ lo, double* out, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = static_cast<double>(hi[i]) + static_cast<double>(lo[i]);
+}
+
+}  // namespace
+
+void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, const MixSeg* segs, int* err,
+                       cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(mixed_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr = true;
+  }
+  if (ntiles > 0) mixed_gemm_kernel<<<ntiles, NTHREADS, SMEM_BYTES, st>>>(tiles, probs, segs, err);
+}
+
+void launch_split(const SplitTask* t, int ntask, cudaStream_t st) {
+  if (ntask > 0) split_kernel<<<ntask < 65535 ? ntask : 65535, 256, 0, st>>>(t, ntask);
+}
+
+void launch_df_to_f64(const float* hi, const float* lo, double* out, int64_t n, int grid, cudaStream_t st) {
+  if (n > 0) df_to_f64_kernel<<<grid, 256, 0, st>>>(hi, lo, out, n);
+}
+
+}  // namespace dmrg

@@ -1,0 +1,25 @@
+// Split-BF16 tensor-core path (tcgen05 / TMEM) shared by exec_cuda.cu and mixed.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../exec.h"
+
+namespace dmrg {
+
+struct MixTile {
+  int prob, m0, n0, pad;
+};
+
+// launch the grouped split-BF16 GEMM over `ntiles` tiles; err is a device int
+// that receives a nonzero code when a bounded wait gives up
+void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, const MixSeg* segs,
+                       int* err, cudaStream_t st);
+void launch_split(const SplitTask* t, int ntask, cudaStream_t st);
+void launch_df_to_f64(const float* hi, const float* lo, double* out, int64_t n, int grid, cudaStream_t st);
+
+constexpr int MIX_TM = 128;   // rows per tile (MMA M)
+constexpr int MIX_TN = 128;   // max columns per tile (MMA N, rounded to 16 per tile)
+
+}  // namespace dmrg
