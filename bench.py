@@ -219,7 +219,9 @@ def main():
         key = "gemm_bf16x"
         peak = pk["bf16_tflops"]
         bound, unit, peak_kind = "tensor", "TFLOP/s", pk_kind
-    kms = prof[key]["ms"] / args.steps if prof[key]["launches"] else None
+    keys = [key] if key == "gemm_f64" else ["gemm_bf16x", "gemm_bf16x_stage1"]
+    kms_tot = sum(prof[k]["ms"] for k in keys)
+    kms = kms_tot / args.steps if kms_tot > 0 else None
     achieved = flops / (kms * 1e-3) / 1e12 if kms else None
     launches = sum(c["launches"] for c in prof.values())
 

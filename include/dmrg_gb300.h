@@ -169,10 +169,12 @@ dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out8);
 
 /* Kernel timing with CUDA events on the handle's stream (this library's
  * kernels only).  mode = 1: reset counters and start; mode = 0: stop and write
- * out12[2c] = milliseconds and out12[2c+1] = launches for the kernel classes
+ * out14[2c] = milliseconds and out14[2c+1] = launches for the kernel classes
  * c = 0 FP64 GEMM, 1 blocking (kron), 2 vector, 3 Jacobi eigen, 4 split-BF16
- * tensor-core GEMM, 5 split/pack.  out12 may be NULL when mode = 1. */
-dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out12);
+ * tensor-core GEMM of sigma stage 2 (and accumulating products), 5 split /
+ * pack / reduce, 6 split-BF16 tensor-core GEMM of sigma stage 1.
+ * out14 may be NULL when mode = 1. */
+dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out14);
 
 void dmrg_destroy(dmrg_handle* h);
 

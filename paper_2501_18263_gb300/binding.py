@@ -20,7 +20,7 @@ PREC_FP64, PREC_MIXED_BF16 = 0, 1
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
            "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sigma_backward", "dmrg_stats",
            "dmrg_profile", "dmrg_destroy", "dmrg_last_error"]
-PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "jacobi", "gemm_bf16x", "split"]
+PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "jacobi", "gemm_bf16x", "split", "gemm_bf16x_stage1"]
 
 
 class DmrgError(RuntimeError):
@@ -177,7 +177,7 @@ class Dmrg:
         self._check(self.lib.dmrg_profile(self.h, 1, None))
 
     def profile_stop(self):
-        o = np.zeros(12)
+        o = np.zeros(14)
         self._check(self.lib.dmrg_profile(self.h, 0, _dp(o)))
         return {c: {"ms": float(o[2 * i]), "launches": int(o[2 * i + 1])} for i, c in enumerate(PROFILE_CLASSES)}
 

@@ -215,6 +215,8 @@ class Engine {
   int psi_split_ = -1;
   std::vector<Chunk> mchunks_;
   int mplan_hl_ = -1;
+  float* part_ = nullptr;
+  int nparts_ = 1;
   void free_mixed();
   // sweep state
   double* psi_cur_ = nullptr;

@@ -698,13 +698,15 @@ std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol) {
     const int D = Dsched ? Dsched[s] : P_.D;
     double e = 0.0, tw = 0.0;
     int iters = 0;
+    // mixed precision: FP64 residual refinement only where the sweep energy is
+    // reported (last step); elsewhere the split-BF16 eigenvector is kept
     for (int b = 0; b <= L - 3; ++b) {   // left to right
-      e = davidson(psi_cur_, tol, 100, 24, &iters, 1);
+      e = davidson(psi_cur_, tol, 100, 24, &iters, 0);
       sweep_log_.push_back({s, b, 1, e, iters});
       truncate_and_move(true, D, &tw);
     }
     for (int b = L - 2; b >= 1; --b) {   // right to left
-      e = davidson(psi_cur_, tol, 100, 24, &iters, 1);
+      e = davidson(psi_cur_, tol, 100, 24, &iters, b == 1 ? 1 : 0);
       sweep_log_.push_back({s, b, 0, e, iters});
       truncate_and_move(false, D, &tw);
     }

@@ -81,7 +81,7 @@ void Engine::free_mixed() {
     if (*p) ex_->release(*p);
     *p = nullptr;
   }
-  for (float** p : {&shi_, &slo_}) {
+  for (float** p : {&shi_, &slo_, &part_}) {
     if (*p) ex_->release(*p);
     *p = nullptr;
   }
@@ -488,8 +488,25 @@ void Engine::build_sigma_plan() {
       }
       xmsize[n] = o;
     }
+    // one X buffer for all terms unless it exceeds the cap (3 BF16 planes per element)
+    const int64_t xcap_m = P_.mem_cap ? std::max<int64_t>(int64_t(1) << 24, int64_t(P_.mem_cap / 2 / 6))
+                                      : int64_t(1) << 33;
+    std::vector<std::pair<size_t, size_t>> mranges;
+    {
+      size_t st0 = 0;
+      int64_t acc = 0;
+      for (size_t n = 0; n < T.size(); ++n) {
+        if (acc + xmsize[n] > xcap_m && n > st0) {
+          mranges.push_back({st0, n});
+          st0 = n;
+          acc = 0;
+        }
+        acc += xmsize[n];
+      }
+      mranges.push_back({st0, T.size()});
+    }
     int64_t xmax_m = 0;
-    for (auto& rg : ranges) {
+    for (auto& rg : mranges) {
       int64_t a = 0;
       for (size_t n = rg.first; n < rg.second; ++n) a += xmsize[n];
       xmax_m = std::max(xmax_m, a);
@@ -498,8 +515,12 @@ void Engine::build_sigma_plan() {
     xpl_ = static_cast<uint16_t*>(ex_->alloc(size_t(3 * xpl_ps_) * sizeof(uint16_t)));
     shi_ = static_cast<float*>(ex_->alloc(psi_n_ * sizeof(float)));
     slo_ = static_cast<float*>(ex_->alloc(psi_n_ * sizeof(float)));
-    for (size_t ci = 0; ci < ranges.size(); ++ci) {
-      const size_t n0 = ranges[ci].first, n1 = ranges[ci].second;
+    // split-K partial sums of stage 2 (double-float pairs), reduced in a fixed order
+    const int kMaxParts = 16;
+    part_ = static_cast<float*>(ex_->alloc(size_t(kMaxParts) * 2 * psi_n_ * sizeof(float)));
+    nparts_ = 1;
+    for (size_t ci = 0; ci < mranges.size(); ++ci) {
+      const size_t n0 = mranges[ci].first, n1 = mranges[ci].second;
       std::vector<int64_t> xb0(T.size(), 0);
       {
         int64_t a = 0;
@@ -538,21 +559,15 @@ void Engine::build_sigma_plan() {
           P1.push_back(q);
         }
       }
-      std::vector<MixProb> P2;
-      std::vector<MixSeg> S2;
+      // segments of every sigma block, then split each block's K list into parts
+      struct Blk2 { int iT, jT; std::vector<MixSeg> segs; int64_t K = 0; int tiles = 0; };
+      std::vector<Blk2> blks;
       for (size_t iT = 0; iT < EL.coarse.q.size(); ++iT) {
         if (psi_off_[iT] < 0) continue;
         const int jT = psi_rcoarse_[iT];
-        MixProb q{};
-        q.Chi = shi_ + psi_off_[iT];
-        q.Clo = slo_ + psi_off_[iT];
-        q.ldc = ER.coarse.dim[jT];
-        q.M = EL.coarse.dim[iT];
-        q.N = ER.coarse.dim[jT];
-        q.alpha = 1.0f;
-        q.mode = 0;
-        q.accumulate = ci > 0;
-        q.s0 = int(S2.size());
+        Blk2 bk;
+        bk.iT = int(iT);
+        bk.jT = jT;
         for (size_t n = n0; n < n1; ++n) {
           const Term& t = T[n];
           QN dR = t.Rt ? QN{0, 0} - t.R->delta : t.R->delta;
@@ -564,15 +579,47 @@ void Engine::build_sigma_plan() {
           const uint16_t* B = oplR_ + (t.Rt ? it->second.second : it->second.first);
           if (!t.L) {
             if (jR != jT) continue;
-            S2.push_back(MixSeg{psiN_ + nOff[iT], B, psN_ps_, opsR_, colpad[jT], colpad[jT], colpad[jT], 0});
+            bk.segs.push_back(MixSeg{psiN_ + nOff[iT], B, psN_ps_, opsR_, colpad[jT], colpad[jT], colpad[jT], 0});
           } else {
             const int xi = xidx[n][iT];
             if (xi < 0 || xl[n][xi].jR != jR) continue;
-            S2.push_back(MixSeg{xpl_ + xb0[n] + xmoff[n][xi], B, xpl_ps_, opsR_, colpad[jR], colpad[jR], colpad[jR], 0});
+            bk.segs.push_back(MixSeg{xpl_ + xb0[n] + xmoff[n][xi], B, xpl_ps_, opsR_, colpad[jR], colpad[jR], colpad[jR], 0});
           }
+          bk.K += colpad[jR];
         }
-        q.s1 = int(S2.size());
-        P2.push_back(q);
+        bk.tiles = ((EL.coarse.dim[iT] + 127) / 128) * ((ER.coarse.dim[jT] + 127) / 128);
+        blks.push_back(std::move(bk));
+      }
+      double work = 0;
+      for (auto& bk : blks) work += double(bk.tiles) * double(bk.K);
+      const double per_cta = std::max(1.0, work / (8.0 * 152.0));
+      std::vector<MixProb> P2;
+      std::vector<MixSeg> S2;
+      for (auto& bk : blks) {
+        int parts = int(std::ceil(double(bk.K) / per_cta));
+        parts = std::max(1, std::min(kMaxParts, std::min(parts, int(bk.segs.size()))));
+        nparts_ = std::max(nparts_, parts);
+        size_t sidx = 0;
+        int64_t done = 0;
+        for (int pp = 0; pp < parts; ++pp) {
+          const int64_t goal = bk.K * (pp + 1) / parts;
+          MixProb q{};
+          q.Chi = part_ + int64_t(pp) * 2 * psi_n_ + psi_off_[bk.iT];
+          q.Clo = q.Chi + psi_n_;
+          q.ldc = ER.coarse.dim[bk.jT];
+          q.M = EL.coarse.dim[bk.iT];
+          q.N = ER.coarse.dim[bk.jT];
+          q.alpha = 1.0f;
+          q.mode = 0;
+          q.accumulate = 0;
+          q.s0 = int(S2.size());
+          while (sidx < bk.segs.size() && (done < goal || pp == parts - 1)) {
+            done += bk.segs[sidx].K;
+            S2.push_back(bk.segs[sidx++]);
+          }
+          q.s1 = int(S2.size());
+          P2.push_back(q);
+        }
       }
       Chunk ch;
       ch.plan1 = P1.empty() ? -1 : ex_->mix_plan(P1, S1);
@@ -704,9 +751,11 @@ void Engine::sigma_precision(const double* psi, double* sig, int precision) {
   }
   ex_->d2d(psi_in_, psi, psi_n_ * sizeof(double));
   ex_->split_run(psi_split_);
-  for (auto& c : mchunks_) {
-    if (c.plan1 >= 0) ex_->mix_run(c.plan1);
-    ex_->mix_run(c.plan2);
+  for (size_t c = 0; c < mchunks_.size(); ++c) {
+    if (mchunks_[c].plan1 >= 0) ex_->mix_run(mchunks_[c].plan1);
+    ex_->zero(part_, size_t(nparts_) * 2 * psi_n_ * sizeof(float));
+    ex_->mix_run(mchunks_[c].plan2);
+    ex_->reduce_parts(part_, nparts_, psi_n_, shi_, slo_, c > 0);
   }
   if (mplan_hl_ >= 0) ex_->mix_run(mplan_hl_);
   ex_->df_to_f64(shi_, slo_, sig, psi_n_);

@@ -131,16 +131,19 @@ class Exec {
   virtual void split_run(int plan) = 0;
   virtual void split_plan_free(int plan) = 0;
   virtual void df_to_f64(const float* hi, const float* lo, double* out, int64_t n) = 0;
+  // (hi, lo)[i] (+)= sum_q part[q] (double-float pairs: part + q*2n holds n hi then n lo)
+  virtual void reduce_parts(const float* part, int nparts, int64_t n, float* hi, float* lo, int accumulate) = 0;
   // nonzero when a bounded device-side wait gave up (read with a stream sync)
   virtual int device_error() = 0;
 
   // kernel timing with events on the stream: mode 1 resets and starts, mode 0 stops
   // and fills out[2*c] = milliseconds, out[2*c+1] = launches for each kernel class c
-  // (0 gemm_f64, 1 kron, 2 vector, 3 syev/ritz, 4 mixed gemm, 5 split/pack)
+  // (0 gemm_f64, 1 kron, 2 vector, 3 syev/ritz, 4 mixed gemm stage 2 / accumulate,
+  //  5 split/pack/reduce, 6 mixed gemm stage 1 (BF16-plane output))
   virtual void profile(int mode, double* out) = 0;
 };
 
-enum { PROF_GEMM = 0, PROF_KRON, PROF_VEC, PROF_EIG, PROF_MIXED, PROF_SPLIT, PROF_N };
+enum { PROF_GEMM = 0, PROF_KRON, PROF_VEC, PROF_EIG, PROF_MIXED, PROF_SPLIT, PROF_MIXED1, PROF_N };
 
 Exec* make_cuda_exec(void* stream, int precision_mode);
 

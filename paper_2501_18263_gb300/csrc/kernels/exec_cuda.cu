@@ -588,6 +588,7 @@ class CudaExec : public Exec {
     MixProb* probs = nullptr;
     MixSeg* segs = nullptr;
     int ntiles = 0;
+    int cls = PROF_MIXED;
     bool live = false;
   };
   struct SplitPlanD {
@@ -615,6 +616,7 @@ class CudaExec : public Exec {
     pl.probs = upload(p);
     pl.segs = upload(s);
     pl.live = true;
+    pl.cls = (!p.empty() && p[0].mode == 1) ? PROF_MIXED1 : PROF_MIXED;
     for (size_t i = 0; i < mplans_.size(); ++i)
       if (!mplans_[i].live) {
         mplans_[i] = pl;
@@ -626,7 +628,7 @@ class CudaExec : public Exec {
   void mix_run(int id) override {
     MixPlanD& pl = mplans_.at(id);
     if (!pl.ntiles) return;
-    launch(PROF_MIXED, [&] { launch_mixed_gemm(pl.tiles, pl.ntiles, pl.probs, pl.segs, err_, st_); });
+    launch(pl.cls, [&] { launch_mixed_gemm(pl.tiles, pl.ntiles, pl.probs, pl.segs, err_, st_); });
   }
   void mix_plan_free(int id) override { mix_free(id); }
   void split_plan_free(int id) override {
@@ -663,6 +665,9 @@ class CudaExec : public Exec {
   }
   void df_to_f64(const float* hi, const float* lo, double* out, int64_t n) override {
     launch(PROF_SPLIT, [&] { launch_df_to_f64(hi, lo, out, n, grid_for(n), st_); });
+  }
+  void reduce_parts(const float* part, int nparts, int64_t n, float* hi, float* lo, int accumulate) override {
+    launch(PROF_SPLIT, [&] { launch_reduce_parts(part, nparts, n, hi, lo, accumulate, grid_for(n), st_); });
   }
   int device_error() override {
     int h = 0;

@@ -65,16 +65,19 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
 
 // bounded wait: gives up after WAIT_CYCLES or when another role aborted
 __device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* err, int code) {
+  if (mbar_try(a, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try(a, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
-      *abort_flag = 1;
-      atomicExch(err, code);
-      return false;
+  for (unsigned spin = 1;; ++spin) {
+    if (mbar_try(a, parity)) return true;
+    if ((spin & 255u) == 0) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > WAIT_CYCLES) {
+        *abort_flag = 1;
+        atomicExch(err, code);
+        return false;
+      }
     }
   }
-  return true;
 }
 
 // shared-memory matrix descriptor: canonical K-major layout without swizzle,
@@ -333,6 +336,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           continue;
         }
         if (gm >= p.M) continue;
+        if (p.mode == 1 && c0 + 16 <= Nt) {
+          // 16 consecutive BF16 per plane: two 16-byte stores each (row starts and
+          // column offsets are multiples of 8 elements in every plane layout)
+          uint32_t h[8], m[8], l[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            uint16_t hh[2], mm[2], ll[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const float a0 = p.alpha * sh[2 * i + u], a1 = p.alpha * sl[2 * i + u];
+              const __nv_bfloat16 bh = __float2bfloat16_rn(a0);
+              const float r = (a0 - __bfloat162float(bh)) + a1;
+              const __nv_bfloat16 bm = __float2bfloat16_rn(r);
+              const __nv_bfloat16 bl = __float2bfloat16_rn(r - __bfloat162float(bm));
+              hh[u] = bf_bits(bh);
+              mm[u] = bf_bits(bm);
+              ll[u] = bf_bits(bl);
+            }
+            h[i] = hh[0] | (uint32_t(hh[1]) << 16);
+            m[i] = mm[0] | (uint32_t(mm[1]) << 16);
+            l[i] = ll[0] | (uint32_t(ll[1]) << 16);
+          }
+          uint16_t* dst = p.Cp + int64_t(gm) * p.ldc + tl.n0 + c0;
+          uint4* d0 = reinterpret_cast<uint4*>(dst);
+          uint4* d1 = reinterpret_cast<uint4*>(dst + p.psC);
+          uint4* d2 = reinterpret_cast<uint4*>(dst + 2 * p.psC);
+          d0[0] = make_uint4(h[0], h[1], h[2], h[3]);
+          d0[1] = make_uint4(h[4], h[5], h[6], h[7]);
+          d1[0] = make_uint4(m[0], m[1], m[2], m[3]);
+          d1[1] = make_uint4(m[4], m[5], m[6], m[7]);
+          d2[0] = make_uint4(l[0], l[1], l[2], l[3]);
+          d2[1] = make_uint4(l[4], l[5], l[6], l[7]);
+          continue;
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           if (c0 + i >= Nt) break;
@@ -418,6 +455,31 @@ __global__ void split_kernel(const SplitTask* __restrict__ t, int nt) {
   }
 }
 
+// sigma = sum over split-K parts p (fixed order) of the double-float partials
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int nparts, int64_t n, float* hi, float* lo,
+                                    int accumulate) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    float sh = part[i], sl = part[n + i];
+    if (accumulate) {
+      float s, e;
+      two_sum(hi[i], sh, s, e);
+      e += lo[i] + sl;
+      sh = s + e;
+      sl = e - (sh - s);
+    }
+    for (int q = 1; q < nparts; ++q) {
+      const float* pq = part + int64_t(q) * 2 * n;
+      float s, e;
+      two_sum(sh, pq[i], s, e);
+      e += sl + pq[n + i];
+      sh = s + e;
+      sl = e - (sh - s);
+    }
+    hi[i] = sh;
+    lo[i] = sl;
+  }
+}
+
 __global__ void df_to_f64_kernel(const float* __restrict__ hi, const float* __restrict__ lo, double* out, int64_t n) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     out[i] = static_cast<double>(hi[i]) + static_cast<double>(lo[i]);
@@ -437,6 +499,11 @@ void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, c
 
 void launch_split(const SplitTask* t, int ntask, cudaStream_t st) {
   if (ntask > 0) split_kernel<<<ntask < 65535 ? ntask : 65535, 256, 0, st>>>(t, ntask);
+}
+
+void launch_reduce_parts(const float* part, int nparts, int64_t n, float* hi, float* lo, int accumulate, int grid,
+                         cudaStream_t st) {
+  if (n > 0) reduce_parts_kernel<<<grid, 256, 0, st>>>(part, nparts, n, hi, lo, accumulate);
 }
 
 void launch_df_to_f64(const float* hi, const float* lo, double* out, int64_t n, int grid, cudaStream_t st) {

@@ -17,6 +17,8 @@ struct MixTile {
 void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, const MixSeg* segs,
                        int* err, cudaStream_t st);
 void launch_split(const SplitTask* t, int ntask, cudaStream_t st);
+void launch_reduce_parts(const float* part, int nparts, int64_t n, float* hi, float* lo, int accumulate, int grid,
+                         cudaStream_t st);
 void launch_df_to_f64(const float* hi, const float* lo, double* out, int64_t n, int grid, cudaStream_t st);
 
 constexpr int MIX_TM = 128;   // rows per tile (MMA M)
