@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--D", type=int, default=2048)
     ap.add_argument("--bond", type=int, default=None)
     ap.add_argument("--seed", type=int, default=3)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 sigma steps timed beside the mixed ones")
     ap.add_argument("--cpu-sample", default="12,6,6,256", help="L,na,nb,D of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     a = ap.parse_args()
@@ -179,11 +180,13 @@ def main():
     clk.start()
     d.profile_start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for _ in range(args.steps):
         d.sigma(args.bond, psi.data_ptr(), sig.data_ptr())
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     prof = d.profile_stop()
     if world > 1:
         dist.barrier()
@@ -194,6 +197,25 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     value = flops * world / (ms * 1e-3) / 1e12
+
+    # the FP64 path on the same handle and operators, timed beside the mixed one
+    fp64 = None
+    if prec == B.PREC_MIXED_BF16 and args.fp64_steps > 0:
+        d.sigma_ex(args.bond, psi.data_ptr(), sig.data_ptr(), B.PREC_FP64)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            d.sigma_ex(args.bond, psi.data_ptr(), sig.data_ptr(), B.PREC_FP64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1) / args.fp64_steps
+        ref64 = sig.clone()
+        d.sigma(args.bond, psi.data_ptr(), sig.data_ptr())
+        torch.cuda.synchronize()
+        relerr = float(torch.linalg.norm(sig - ref64) / torch.linalg.norm(ref64))
+        fp64 = {"value": round(flops / (fms * 1e-3) / 1e12, 4), "unit": "TFLOP/s", "ms_per_step": round(fms, 3),
+                "steps": args.fp64_steps, "mixed_vs_fp64_rel_err": relerr}
 
     # end to end through the public host-buffer entry point
     psi_h = np.ascontiguousarray(B.pack_psi(bp.psi))
@@ -257,6 +279,7 @@ def main():
                      "kernel": key, "peak_source": peak_kind,
                      "kernel_ms_per_step": round(kms, 3) if kms else None},
         "profile_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]},
+        "fp64": fp64,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         def flops_of(t_, v_, na_, nb_, D_, bp_, bond_):

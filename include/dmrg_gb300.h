@@ -118,6 +118,10 @@ dmrg_status dmrg_layout(dmrg_handle* h, int32_t bond, int32_t* n_blocks, const i
 /* sigma = H_eff psi at `bond` (device buffers of psi_size doubles). */
 dmrg_status dmrg_sigma(dmrg_handle* h, int32_t bond, const double* psi_dev, double* sigma_dev);
 
+/* sigma at an explicit precision (DMRG_PREC_*): DMRG_PREC_FP64 is available on
+ * every handle; DMRG_PREC_MIXED_BF16 needs a handle created with it. */
+dmrg_status dmrg_sigma_ex(dmrg_handle* h, int32_t bond, const double* psi_dev, double* sigma_dev, int32_t precision);
+
 /* Same with host buffers: host->device copy of psi, sigma, device->host copy. */
 dmrg_status dmrg_sigma_host(dmrg_handle* h, int32_t bond, const double* psi_host, double* sigma_host);
 

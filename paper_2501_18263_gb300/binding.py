@@ -18,7 +18,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOCONV, ERR_NONFINITE, ERR_STAT
 PREC_FP64, PREC_MIXED_BF16 = 0, 1
 
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
-           "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sigma_backward", "dmrg_stats",
+           "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sigma_backward", "dmrg_stats",
            "dmrg_profile", "dmrg_destroy", "dmrg_last_error"]
 PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "jacobi", "gemm_bf16x", "split", "gemm_bf16x_stage1"]
 
@@ -54,6 +54,7 @@ def load_library(path: str | None = None):
         "dmrg_prepare": ([vp, i32], ctypes.c_int),
         "dmrg_layout": ([vp, i32, ip, ctypes.POINTER(i64p), i64p], ctypes.c_int),
         "dmrg_sigma": ([vp, i32, vp, vp], ctypes.c_int),
+        "dmrg_sigma_ex": ([vp, i32, vp, vp, i32], ctypes.c_int),
         "dmrg_sigma_host": ([vp, i32, dp, dp], ctypes.c_int),
         "dmrg_sigma_host_noalloc": ([vp, i32, dp, dp], ctypes.c_int),
         "dmrg_davidson": ([vp, i32, vp, f64, i32, dp, ip], ctypes.c_int),
@@ -135,6 +136,10 @@ class Dmrg:
     # -- compute
     def sigma(self, bond, psi_ptr, sig_ptr):
         self._check(self.lib.dmrg_sigma(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.c_void_p(int(sig_ptr))))
+
+    def sigma_ex(self, bond, psi_ptr, sig_ptr, precision):
+        self._check(self.lib.dmrg_sigma_ex(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.c_void_p(int(sig_ptr)),
+                                           int(precision)))
 
     def sigma_host(self, bond, psi):
         psi = np.ascontiguousarray(psi, dtype=np.float64)

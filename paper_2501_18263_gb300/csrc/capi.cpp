@@ -205,6 +205,20 @@ dmrg_status dmrg_sigma(dmrg_handle* h, int32_t bond, const double* psi, double* 
   });
 }
 
+dmrg_status dmrg_sigma_ex(dmrg_handle* h, int32_t bond, const double* psi, double* sig, int32_t precision) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !psi || !sig) return fail(DMRG_ERR_ARG, "null argument");
+    if (precision != DMRG_PREC_FP64 && precision != DMRG_PREC_MIXED_BF16) return fail(DMRG_ERR_ARG, "unknown precision");
+    if (precision == DMRG_PREC_MIXED_BF16 && h->eng->problem().precision != DMRG_PREC_MIXED_BF16)
+      return fail(DMRG_ERR_ARG, "the handle was not created with the split-BF16 precision");
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    h->eng->sigma_precision(psi, sig, precision);
+    h->eng->exec()->sync();
+    return check_device(h);
+  });
+}
+
 dmrg_status dmrg_sigma_host(dmrg_handle* h, int32_t bond, const double* psi, double* sig) {
   return guard([&]() -> dmrg_status {
     if (!h || !psi || !sig) return fail(DMRG_ERR_ARG, "null argument");

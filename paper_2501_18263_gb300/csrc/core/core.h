@@ -204,7 +204,8 @@ class Engine {
   bool mixed_ready_ = false;
   uint16_t* oplL_ = nullptr;
   uint16_t* oplR_ = nullptr;
-  int64_t opsL_ = 0, opsR_ = 0;
+  uint16_t* oplLf_ = nullptr;   // fine (per sub-block) planes of the L' operators
+  int64_t opsL_ = 0, opsR_ = 0, opsLf_ = 0;
   uint16_t* psiT_ = nullptr;
   uint16_t* psiN_ = nullptr;
   int64_t psT_ps_ = 0, psN_ps_ = 0;

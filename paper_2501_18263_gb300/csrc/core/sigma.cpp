@@ -77,7 +77,7 @@ void Engine::free_mixed() {
   mplan_hl_ = -1;
   if (psi_split_ >= 0) ex_->split_plan_free(psi_split_);
   psi_split_ = -1;
-  for (uint16_t** p : {&oplL_, &oplR_, &psiT_, &psiN_, &xpl_}) {
+  for (uint16_t** p : {&oplL_, &oplR_, &oplLf_, &psiT_, &psiN_, &xpl_}) {
     if (*p) ex_->release(*p);
     *p = nullptr;
   }
@@ -437,6 +437,29 @@ void Engine::build_sigma_plan() {
     };
     planes(EopsL_, EL, rowpad, rp, offL, oplL_, opsL_);
     planes(EopsR_, ER, colpad, cp, offR, oplR_, opsR_);
+    // fine planes of the L' operators for stage 1: every nonzero sub-block alone,
+    // normal (rows x pad8(cols)) and transposed (cols x pad8(rows))
+    {
+      int64_t o = 0;
+      for (auto& kv : EopsL_.ops)
+        for (auto& bk : kv.second.blk) {
+          bk.pn = o;
+          o += int64_t(bk.rows) * pad8(bk.cols);
+          bk.pt = o;
+          o += int64_t(bk.cols) * pad8(bk.rows);
+        }
+      opsLf_ = pad8(o) + 8;
+      oplLf_ = static_cast<uint16_t*>(ex_->alloc(size_t(3 * opsLf_) * sizeof(uint16_t)));
+      ex_->zero(oplLf_, size_t(3 * opsLf_) * sizeof(uint16_t));
+      std::vector<SplitTask> tk;
+      for (auto& kv : EopsL_.ops)
+        for (auto& bk : kv.second.blk)
+          tk.push_back(SplitTask{EopsL_.arena + bk.off, bk.rows, bk.cols, bk.cols, int(pad8(bk.cols)),
+                                 int(pad8(bk.rows)), 0, oplLf_ + bk.pn, oplLf_ + bk.pt, opsLf_});
+      int sp = ex_->split_plan(tk);
+      ex_->split_run(sp);
+      ex_->split_plan_free(sp);
+    }
     // psi planes: psiN (rows x colpad), psiT (colpad x rowpad), psiTu (cols x rowpad)
     std::vector<int64_t> tOff(EL.coarse.q.size(), -1), nOff(EL.coarse.q.size(), -1), uOff(EL.coarse.q.size(), -1);
     int64_t tT = 0, tN = 0, tU = 0;
@@ -529,8 +552,19 @@ void Engine::build_sigma_plan() {
           a += xmsize[n];
         }
       }
+      // Stage 1 on nonzero fine sub-blocks, as transposed tiles (tile rows run over
+      // the padded R' columns of X, tile columns over rows of X).  A row block ft of
+      // X_nu that receives a single fine block (ft <- f) -- every normal operator,
+      // by its Kronecker form -- joins the gathered problem of (psi block, f): all
+      // such rows of all terms share the A operand psi^T{jR, f} and become columns
+      // of one wide GEMM (B rows and output rows from per-column tables).  Rows
+      // with several contributing f (complementary S_q) are separate problems.
       std::vector<MixProb> P1;
       std::vector<MixSeg> S1;
+      std::vector<int64_t> bcol, ccol;
+      std::vector<float> acol;
+      struct GCol { int64_t b, c; float a; };
+      std::map<std::tuple<int, int, int>, std::vector<GCol>> groups;   // (iL, jR, f) -> columns
       for (size_t n = n0; n < n1; ++n) {
         const Term& t = T[n];
         if (!t.L) continue;
@@ -538,26 +572,67 @@ void Engine::build_sigma_plan() {
           const XBlk& xb = xl[n][k];
           const QN qL = EL.coarse.q[xb.iL];
           const double sg = (t.R && t.R->odd && (qL.n() & 1)) ? -1.0 : 1.0;
-          MixProb q{};
-          q.Cp = xpl_ + xb0[n] + xmoff[n][k];
-          q.psC = xpl_ps_;
-          q.ldc = colpad[xb.jR];
-          q.M = EL.coarse.dim[xb.iT];
-          q.N = colpad[xb.jR];
-          q.alpha = float(t.c * sg);
-          q.mode = 1;
-          q.accumulate = 0;
-          q.s0 = int(S1.size());
-          const CKey key = t.Lt ? CKey{t.L, xb.iL, xb.iT} : CKey{t.L, xb.iT, xb.iL};
-          auto it = offL.find(key);
-          if (it != offL.end()) {
-            const int64_t o = t.Lt ? it->second.second : it->second.first;
-            S1.push_back(MixSeg{oplL_ + o, psiT_ + tOff[xb.iL], opsL_, psT_ps_, rowpad[xb.iL], rowpad[xb.iL],
-                                rowpad[xb.iL], 0});
+          const int cpj = colpad[xb.jR];
+          const int64_t xoff = xb0[n] + xmoff[n][k];
+          for (int ft : EL.coarse_fines[xb.iT]) {
+            std::vector<std::pair<int, const OpBlk*>> fs;
+            for (int f : EL.coarse_fines[xb.iL]) {
+              auto it = t.Lt ? fmL[n].find({f, ft}) : fmL[n].find({ft, f});
+              if (it != fmL[n].end()) fs.push_back({f, it->second});
+            }
+            if (fs.size() == 1) {
+              const int f = fs[0].first;
+              const OpBlk* ob = fs[0].second;
+              const int64_t b0 = t.Lt ? ob->pt : ob->pn;
+              auto& col = groups[std::make_tuple(xb.iL, xb.jR, f)];
+              for (int j = 0; j < EL.f_dim[ft]; ++j)
+                col.push_back(GCol{b0 + int64_t(j) * pad8(EL.f_dim[f]), xoff + int64_t(EL.f_row[ft] + j) * cpj,
+                                   float(t.c * sg)});
+              continue;
+            }
+            MixProb q{};
+            q.Cp = xpl_ + xoff + int64_t(EL.f_row[ft]) * cpj;
+            q.psC = xpl_ps_;
+            q.ldc = cpj;
+            q.M = cpj;
+            q.N = EL.f_dim[ft];
+            q.alpha = float(t.c * sg);
+            q.mode = 2;
+            q.accumulate = 0;
+            q.cm0 = -1;
+            q.s0 = int(S1.size());
+            for (auto& fb : fs) {
+              const int f = fb.first;
+              const uint16_t* Bp = oplLf_ + (t.Lt ? fb.second->pt : fb.second->pn);
+              S1.push_back(MixSeg{psiT_ + tOff[xb.iL] + rp[f], Bp, psT_ps_, opsLf_, rowpad[xb.iL],
+                                  int(pad8(EL.f_dim[f])), EL.f_dim[f], 0});
+            }
+            q.s1 = int(S1.size());
+            P1.push_back(q);
           }
-          q.s1 = int(S1.size());
-          P1.push_back(q);
         }
+      }
+      for (auto& gk : groups) {
+        const int iL = std::get<0>(gk.first), jR = std::get<1>(gk.first), f = std::get<2>(gk.first);
+        MixProb q{};
+        q.Cp = xpl_;
+        q.psC = xpl_ps_;
+        q.ldc = colpad[jR];
+        q.M = colpad[jR];
+        q.N = int(gk.second.size());
+        q.alpha = 1.0f;
+        q.mode = 3;
+        q.accumulate = 0;
+        q.cm0 = int64_t(bcol.size());
+        for (const GCol& c : gk.second) {
+          bcol.push_back(c.b);
+          ccol.push_back(c.c);
+          acol.push_back(c.a);
+        }
+        q.s0 = int(S1.size());
+        S1.push_back(MixSeg{psiT_ + tOff[iL] + rp[f], oplLf_, psT_ps_, opsLf_, rowpad[iL], 8, EL.f_dim[f], 0});
+        q.s1 = int(S1.size());
+        P1.push_back(q);
       }
       // segments of every sigma block, then split each block's K list into parts
       struct Blk2 { int iT, jT; std::vector<MixSeg> segs; int64_t K = 0; int tiles = 0; };
@@ -622,7 +697,7 @@ void Engine::build_sigma_plan() {
         }
       }
       Chunk ch;
-      ch.plan1 = P1.empty() ? -1 : ex_->mix_plan(P1, S1);
+      ch.plan1 = P1.empty() ? -1 : ex_->mix_plan_g(P1, S1, bcol, ccol, acol);
       ch.plan2 = ex_->mix_plan(P2, S2);
       mchunks_.push_back(ch);
     }

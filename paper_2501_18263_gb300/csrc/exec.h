@@ -62,6 +62,9 @@ struct MixSeg {
 // C (M x N) = alpha * sum_seg A_seg B_seg^T
 //   mode 0: C kept as a float pair (hi, lo) at Chi/Clo (+= if accumulate)
 //   mode 1: C written as three BF16 planes at Cp (plane stride psC)
+//   mode 2: as mode 1 but transposed: tile column n is written to row n of C
+//   mode 3: gathered columns: column n takes its B row at B + bcol[cm0 + n] and is
+//           written (transposed, scaled by acol[cm0 + n]) to Cp + ccol[cm0 + n]
 struct MixProb {
   float* Chi;
   float* Clo;
@@ -70,6 +73,7 @@ struct MixProb {
   int ldc, M, N, s0, s1;
   float alpha;
   int mode, accumulate;
+  int64_t cm0;
 };
 // FP64 block (rows x cols, ld) -> BF16 planes, normal (rows x ldn) and/or transposed (cols x ldt)
 struct SplitTask {
@@ -125,6 +129,10 @@ class Exec {
 
   // split-BF16 tensor-core GEMM plans (tcgen05 / TMEM)
   virtual int mix_plan(const std::vector<MixProb>& p, const std::vector<MixSeg>& s) = 0;
+  // plan with the per-column tables of mode-3 problems
+  virtual int mix_plan_g(const std::vector<MixProb>& p, const std::vector<MixSeg>& s,
+                         const std::vector<int64_t>& bcol, const std::vector<int64_t>& ccol,
+                         const std::vector<float>& acol) = 0;
   virtual void mix_run(int plan) = 0;
   virtual void mix_plan_free(int plan) = 0;
   virtual int split_plan(const std::vector<SplitTask>& t) = 0;

@@ -587,6 +587,9 @@ class CudaExec : public Exec {
     MixTile* tiles = nullptr;
     MixProb* probs = nullptr;
     MixSeg* segs = nullptr;
+    int64_t* bcol = nullptr;
+    int64_t* ccol = nullptr;
+    float* acol = nullptr;
     int ntiles = 0;
     int cls = PROF_MIXED;
     bool live = false;
@@ -601,22 +604,46 @@ class CudaExec : public Exec {
   int* err_ = nullptr;
 
   int mix_plan(const std::vector<MixProb>& p, const std::vector<MixSeg>& s) override {
+    return mix_plan_g(p, s, {}, {}, {});
+  }
+  int mix_plan_g(const std::vector<MixProb>& p, const std::vector<MixSeg>& s, const std::vector<int64_t>& bcol,
+                 const std::vector<int64_t>& ccol, const std::vector<float>& acol) override {
     for (const MixSeg& g : s) {
       if ((reinterpret_cast<uintptr_t>(g.A) & 15) || (reinterpret_cast<uintptr_t>(g.B) & 15) || (g.lda & 7) ||
           (g.ldb & 7) || (g.psA & 7) || (g.psB & 7) || g.K <= 0)
         throw std::runtime_error("mix_plan: operand not 16-byte aligned / padded");
     }
     std::vector<MixTile> tiles;
-    for (size_t i = 0; i < p.size(); ++i)
+    std::vector<int64_t> work;
+    for (size_t i = 0; i < p.size(); ++i) {
+      int64_t w = 1;
+      for (int q = p[i].s0; q < p[i].s1; ++q) w += (s[q].K + 31) / 32;
       for (int m0 = 0; m0 < p[i].M; m0 += MIX_TM)
-        for (int n0 = 0; n0 < p[i].N; n0 += MIX_TN) tiles.push_back(MixTile{int(i), m0, n0, 0});
+        for (int n0 = 0; n0 < p[i].N; n0 += MIX_TN) {
+          tiles.push_back(MixTile{int(i), m0, n0, 0});
+          work.push_back(w);
+        }
+    }
+    {
+      // persistent CTAs take tiles in strides: longest first balances the load
+      std::vector<size_t> ord(tiles.size());
+      for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+      std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+      std::vector<MixTile> t2;
+      t2.reserve(tiles.size());
+      for (size_t i : ord) t2.push_back(tiles[i]);
+      tiles.swap(t2);
+    }
     MixPlanD pl;
     pl.ntiles = int(tiles.size());
     pl.tiles = upload(tiles);
     pl.probs = upload(p);
     pl.segs = upload(s);
+    pl.bcol = upload(bcol);
+    pl.ccol = upload(ccol);
+    pl.acol = upload(acol);
     pl.live = true;
-    pl.cls = (!p.empty() && p[0].mode == 1) ? PROF_MIXED1 : PROF_MIXED;
+    pl.cls = (!p.empty() && p[0].mode != 0) ? PROF_MIXED1 : PROF_MIXED;
     for (size_t i = 0; i < mplans_.size(); ++i)
       if (!mplans_[i].live) {
         mplans_[i] = pl;
@@ -628,7 +655,7 @@ class CudaExec : public Exec {
   void mix_run(int id) override {
     MixPlanD& pl = mplans_.at(id);
     if (!pl.ntiles) return;
-    launch(pl.cls, [&] { launch_mixed_gemm(pl.tiles, pl.ntiles, pl.probs, pl.segs, err_, st_); });
+    launch(pl.cls, [&] { launch_mixed_gemm(pl.tiles, pl.ntiles, pl.probs, pl.segs, pl.bcol, pl.ccol, pl.acol, err_, nsm_, st_); });
   }
   void mix_plan_free(int id) override { mix_free(id); }
   void split_plan_free(int id) override {
@@ -643,6 +670,9 @@ class CudaExec : public Exec {
     cudaFreeAsync(pl.tiles, st_);
     cudaFreeAsync(pl.probs, st_);
     cudaFreeAsync(pl.segs, st_);
+    cudaFreeAsync(pl.bcol, st_);
+    cudaFreeAsync(pl.ccol, st_);
+    cudaFreeAsync(pl.acol, st_);
     pl.live = false;
   }
   int split_plan(const std::vector<SplitTask>& t) override {

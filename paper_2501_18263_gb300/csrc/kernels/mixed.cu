@@ -32,8 +32,11 @@ constexpr int PLANE_BYTES = MIX_TM * BK * 2;    // one 128 x 32 BF16 plane: 8 Ki
 constexpr int STAGE_BYTES = 6 * PLANE_BYTES;    // 3 A planes + 3 B planes
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES;
-constexpr int NTHREADS = 288;
-constexpr int CHUNK = 4;                        // K stages per accumulator drain (128 K)
+constexpr int PRODUCER_WARPS = 3;
+constexpr int PRODUCER_THREADS = 32 * PRODUCER_WARPS;
+constexpr int DRAIN_THREADS = 256;              // 8 warps: 4 lane quarters x 2 column halves
+constexpr int NTHREADS = 32 + PRODUCER_THREADS + DRAIN_THREADS;
+constexpr int CHUNK = 4;                        // K stages per accumulator chunk (128 K)
 constexpr long long WAIT_CYCLES = 4000000000LL; // about 2 s at 2 GHz
 constexpr uint32_t TMEM_COLS = 512;
 
@@ -153,6 +156,10 @@ __device__ __forceinline__ void tmem_st2(uint32_t t0, uint32_t t1, const float* 
       : "memory");
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
 __device__ __forceinline__ uint16_t bf_bits(__nv_bfloat16 x) { return __bfloat16_as_ushort(x); }
 
 // error-free sum of two floats (TwoSum)
@@ -162,35 +169,72 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// double-float value (hi + lo) as three BF16 planes
+__device__ __forceinline__ void split3(float a0, float a1, uint16_t& h, uint16_t& m, uint16_t& l) {
+  const __nv_bfloat16 bh = __float2bfloat16_rn(a0);
+  const float r = (a0 - __bfloat162float(bh)) + a1;
+  const __nv_bfloat16 bm = __float2bfloat16_rn(r);
+  const __nv_bfloat16 bl = __float2bfloat16_rn(r - __bfloat162float(bm));
+  h = bf_bits(bh);
+  m = bf_bits(bm);
+  l = bf_bits(bl);
+}
+
+// two 32-lane x 8-column loads and the wait, in one statement
+__device__ __forceinline__ void tmem_ld2x8(uint32_t t0, uint32_t t1, float* v0, float* v1) {
+  uint32_t a[8], b[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+        "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7])
+      : "r"(t0), "r"(t1)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    v0[i] = __uint_as_float(a[i]);
+    v1[i] = __uint_as_float(b[i]);
+  }
+}
+
+// Persistent split-BF16 grouped GEMM.  Grid = min(#tiles, #SMs); CTA c takes the
+// tiles c, c + G, c + 2G, ... of a list sorted by decreasing work.  12 warps
+// (three per SM sub-partition, so up to 168 registers each):
+//   warp 0        TMEM allocation and the MMA issuer (one lane)
+//   warps 1-3     producers: 16-byte loads of A/B planes into the smem ring
+//   warps 4-11    drain + epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and
+//                 columns 64 ((w - 4) / 4) .. +63 of each accumulator chunk
+// The accumulators are double-buffered per chunk of CHUNK stages: buffer b holds
+// acc0 (hi x hi) in TMEM columns [256 b, 256 b + 128) and acc1 (the five small
+// products) in [256 b + 128, 256 b + 256); while the drain warps fold chunk g
+// into their double-float register sums the MMA warp fills the other buffer.
 __global__ void __launch_bounds__(NTHREADS, 1)
-    mixed_gemm_kernel(const MixTile* __restrict__ tiles, const MixProb* __restrict__ probs,
-                      const MixSeg* __restrict__ segs, int* err) {
+    mixed_gemm_kernel(const MixTile* __restrict__ tiles, int ntiles, const MixProb* __restrict__ probs,
+                      const MixSeg* __restrict__ segs, const int64_t* __restrict__ bcol,
+                      const int64_t* __restrict__ ccol, const float* __restrict__ acol, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // bars: full[STAGES], empty[STAGES], chunk_done, drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+  // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const MixTile tl = tiles[blockIdx.x];
-  const MixProb p = probs[tl.prob];
-  const int Nt = min(MIX_TN, p.N - tl.n0);
-  const int Nmma = (Nt + 15) & ~15;
-  int nsteps = 0;
-  for (int s = p.s0; s < p.s1; ++s) nsteps += (segs[s].K + BK - 1) / BK;
-  const int nchunks = (nsteps + CHUNK - 1) / CHUNK;
+  const int G = gridDim.x;
 
   auto full = [&](int s) { return saddr(&bars[s]); };
   auto empty = [&](int s) { return saddr(&bars[STAGES + s]); };
-  const uint32_t chunk_done = saddr(&bars[2 * STAGES]);
-  const uint32_t drained = saddr(&bars[2 * STAGES + 1]);
+  auto acc_full = [&](int b) { return saddr(&bars[2 * STAGES + b]); };
+  auto acc_empty = [&](int b) { return saddr(&bars[2 * STAGES + 2 + b]); };
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full(s), 128);
+      mbar_init(full(s), PRODUCER_THREADS);
       mbar_init(empty(s), 1);
     }
-    mbar_init(chunk_done, 1);
-    mbar_init(drained, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), DRAIN_THREADS);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -207,214 +251,218 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     // ---- MMA issuer
-    if (lane == 0 && nsteps > 0) {
-      const uint32_t id = idesc(Nmma);
-      int step = 0, in_chunk = 0, chunk = 0;
-      for (int s = p.s0; s < p.s1; ++s) {
-        const int K = segs[s].K;
-        for (int k0 = 0; k0 < K; k0 += BK, ++step) {
-          const int st = step % STAGES;
-          if (in_chunk == 0 && chunk > 0 &&
-              !mbar_wait(drained, (chunk - 1) & 1, abort_flag, err, 4))
-            goto mma_done;
-          if (!mbar_wait(full(st), (step / STAGES) & 1, abort_flag, err, 1)) goto mma_done;
-          fence_after();
-          const uint32_t base = saddr(smem + st * STAGE_BYTES);
-          const int ksub = (K - k0 > 16) ? 2 : 1;
-          for (int kk = 0; kk < ksub; ++kk) {
-            const uint32_t o = kk * 256;
-            const uint64_t a0 = sdesc(base + o), a1 = sdesc(base + PLANE_BYTES + o),
-                           a2 = sdesc(base + 2 * PLANE_BYTES + o);
-            const uint64_t b0 = sdesc(base + 3 * PLANE_BYTES + o), b1 = sdesc(base + 4 * PLANE_BYTES + o),
-                           b2 = sdesc(base + 5 * PLANE_BYTES + o);
-            const uint32_t acc = (in_chunk == 0 && kk == 0) ? 0u : 1u;
-            mma(tmem, a0, b0, id, acc);
-            mma(tmem + 128, a0, b1, id, acc);
-            mma(tmem + 128, a1, b0, id, 1u);
-            mma(tmem + 128, a0, b2, id, 1u);
-            mma(tmem + 128, a1, b1, id, 1u);
-            mma(tmem + 128, a2, b0, id, 1u);
-          }
-          mma_commit(empty(st));
-          if (++in_chunk == CHUNK) {
-            mma_commit(chunk_done);
-            in_chunk = 0;
-            ++chunk;
+    if (lane == 0) {
+      int step = 0;     // global stage counter (ring position)
+      int chunk = 0;    // global chunk counter (accumulator buffer rotation)
+      for (int ti = blockIdx.x; ti < ntiles; ti += G) {
+        const MixTile tl = tiles[ti];
+        const MixProb p = probs[tl.prob];
+        const int Nt = min(MIX_TN, p.N - tl.n0);
+        const uint32_t id = idesc((Nt + 15) & ~15);
+        int in_chunk = 0;
+        uint32_t dbase = 0;
+        for (int s = p.s0; s < p.s1; ++s) {
+          const int K = segs[s].K;
+          for (int k0 = 0; k0 < K; k0 += BK, ++step) {
+            if (in_chunk == 0) {
+              const int b = chunk & 1, use = chunk >> 1;
+              if (use > 0 && !mbar_wait(acc_empty(b), (use - 1) & 1, abort_flag, err, 4)) goto mma_done;
+              dbase = tmem + 256u * b;
+            }
+            const int st = step % STAGES;
+            if (!mbar_wait(full(st), (step / STAGES) & 1, abort_flag, err, 1)) goto mma_done;
+            // the stage was written by cp.async (generic proxy); order it before the
+            // tensor core's async-proxy reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fence_after();
+            const uint32_t base = saddr(smem + st * STAGE_BYTES);
+            const int ksub = (K - k0 > 16) ? 2 : 1;
+            for (int kk = 0; kk < ksub; ++kk) {
+              const uint32_t o = kk * 256;
+              const uint64_t a0 = sdesc(base + o), a1 = sdesc(base + PLANE_BYTES + o),
+                             a2 = sdesc(base + 2 * PLANE_BYTES + o);
+              const uint64_t b0 = sdesc(base + 3 * PLANE_BYTES + o), b1 = sdesc(base + 4 * PLANE_BYTES + o),
+                             b2 = sdesc(base + 5 * PLANE_BYTES + o);
+              const uint32_t acc = (in_chunk == 0 && kk == 0) ? 0u : 1u;
+              mma(dbase, a0, b0, id, acc);
+              mma(dbase + 128, a0, b1, id, acc);
+              mma(dbase + 128, a1, b0, id, 1u);
+              mma(dbase + 128, a0, b2, id, 1u);
+              mma(dbase + 128, a1, b1, id, 1u);
+              mma(dbase + 128, a2, b0, id, 1u);
+            }
+            mma_commit(empty(st));
+            if (++in_chunk == CHUNK) {
+              mma_commit(acc_full(chunk & 1));
+              in_chunk = 0;
+              ++chunk;
+            }
           }
         }
+        if (in_chunk > 0) {
+          mma_commit(acc_full(chunk & 1));
+          ++chunk;
+        }
       }
-      if (in_chunk > 0) mma_commit(chunk_done);
       goto mma_end;
     mma_done:
-      // aborted: release the drain warps waiting for the current chunk
-      mma_commit(chunk_done);
+      *abort_flag = 1;
+      mma_commit(acc_full(chunk & 1));
     mma_end:;
     }
     __syncwarp();
-  } else if (warp <= 4) {
-    // ---- producers: warps 1..4
+  } else if (warp < 1 + PRODUCER_WARPS) {
+    // ---- producers
     const int pt = tid - 32;
     int step = 0;
     bool stop = false;
-    for (int s = p.s0; s < p.s1 && !stop; ++s) {
-      const MixSeg g = segs[s];
-      const int Kp = (g.K + 7) & ~7;
-      for (int k0 = 0; k0 < g.K; k0 += BK, ++step) {
-        const int st = step % STAGES;
-        if (step >= STAGES && !mbar_wait(empty(st), ((step / STAGES) - 1) & 1, abort_flag, err, 2)) {
-          stop = true;
-          break;
+    for (int ti = blockIdx.x; ti < ntiles && !stop; ti += G) {
+      const MixTile tl = tiles[ti];
+      const MixProb p = probs[tl.prob];
+      const int Nt = min(MIX_TN, p.N - tl.n0);
+      const int Nmma = (Nt + 15) & ~15;
+      for (int s = p.s0; s < p.s1 && !stop; ++s) {
+        const MixSeg g = segs[s];
+        const int Kp = (g.K + 7) & ~7;
+        for (int k0 = 0; k0 < g.K; k0 += BK, ++step) {
+          const int st = step % STAGES;
+          if (step >= STAGES && !mbar_wait(empty(st), ((step / STAGES) - 1) & 1, abort_flag, err, 2)) {
+            stop = true;
+            break;
+          }
+          const uint32_t base = saddr(smem + st * STAGE_BYTES);
+          for (int idx = pt; idx < 512; idx += PRODUCER_THREADS) {
+            const int r = idx >> 2, j = idx & 3;
+            const int k = k0 + 8 * j;
+            const uint32_t so = (((r >> 3) * (BK / 8) + j) << 7) + ((r & 7) << 4);
+            const int gm = tl.m0 + r, gn = tl.n0 + r;
+            const bool va = gm < p.M && k < Kp;
+            const bool vb = r < Nmma && gn < p.N && k < Kp;
+            // out-of-range chunks are zero-filled (source size 0, base pointer as a valid address)
+            const uint16_t* a = va ? g.A + int64_t(gm) * g.lda + k : g.A;
+            const uint16_t* bb =
+                vb ? g.B + (p.mode == 3 ? bcol[p.cm0 + gn] : int64_t(gn) * g.ldb) + k : g.B;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              cp_async16(base + q * PLANE_BYTES + so, a + q * g.psA, va ? 16u : 0u);
+              cp_async16(base + (3 + q) * PLANE_BYTES + so, bb + q * g.psB, vb ? 16u : 0u);
+            }
+          }
+          // arrive on full(st) once all of this thread's copies have landed
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full(st)) : "memory");
         }
-        uint8_t* base = smem + st * STAGE_BYTES;
-#pragma unroll
-        for (int it = 0; it < 4; ++it) {
-          const int idx = pt + it * 128;
-          const int r = idx >> 2, j = idx & 3;
-          const int k = k0 + 8 * j;
-          const uint32_t so = (((r >> 3) * (BK / 8) + j) << 7) + ((r & 7) << 4);
-          uint4 va[3], vb[3];
-#pragma unroll
-          for (int q = 0; q < 3; ++q) va[q] = vb[q] = make_uint4(0, 0, 0, 0);
-          const int gm = tl.m0 + r, gn = tl.n0 + r;
-          if (gm < p.M && k < Kp) {
-            const uint16_t* a = g.A + int64_t(gm) * g.lda + k;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) va[q] = __ldg(reinterpret_cast<const uint4*>(a + q * g.psA));
-          }
-          if (r < Nmma && gn < p.N && k < Kp) {
-            const uint16_t* b = g.B + int64_t(gn) * g.ldb + k;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) vb[q] = __ldg(reinterpret_cast<const uint4*>(b + q * g.psB));
-          }
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            *reinterpret_cast<uint4*>(base + q * PLANE_BYTES + so) = va[q];
-            *reinterpret_cast<uint4*>(base + (3 + q) * PLANE_BYTES + so) = vb[q];
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(full(st));
       }
     }
   } else {
-    // ---- drain + epilogue: warps 5..8, TMEM lane quarter warp % 4
-    const int q4 = warp & 3;
+    // ---- drain + epilogue
+    const int dw = warp - 1 - PRODUCER_WARPS;   // 0..7
+    const int q4 = warp & 3;                     // TMEM lane quarter of this warp
+    const int ch = dw >> 2;                      // column half: columns [64 ch, 64 ch + 64)
     const int row = q4 * 32 + lane;
-    const int gm = tl.m0 + row;
-    const uint32_t lb = tmem + (static_cast<uint32_t>(q4 * 32) << 16);
+    const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
+    int chunk = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      if (ok) ok = mbar_wait(chunk_done, c & 1, abort_flag, err, 3);
-      ok = __all_sync(0xffffffffu, ok);
-      fence_after();
-      const bool last = (c == nchunks - 1);
-      for (int c0 = 0; c0 < Nmma; c0 += 16) {
-        float v0[16], v1[16], sh[16], sl[16];
-        if (ok) {
-          tmem_ld2(lb + c0, lb + 128 + c0, v0, v1);
-          if (c > 0) tmem_ld2(lb + 256 + c0, lb + 384 + c0, sh, sl);
-        } else {
+    for (int ti = blockIdx.x; ti < ntiles; ti += G) {
+      const MixTile tl = tiles[ti];
+      const MixProb p = probs[tl.prob];
+      const int Nt = min(MIX_TN, p.N - tl.n0);
+      const int Nmma = (Nt + 15) & ~15;
+      int nsteps = 0;
+      for (int s = p.s0; s < p.s1; ++s) nsteps += (segs[s].K + BK - 1) / BK;
+      const int nch = (nsteps + CHUNK - 1) / CHUNK;
+      float sh[64], sl[64];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v0[i] = v1[i] = 0.f;
+      for (int i = 0; i < 64; ++i) sh[i] = sl[i] = 0.f;
+      const bool mine = 64 * ch < Nmma;          // this warp's columns exist in the tile
+      for (int c = 0; c < nch; ++c, ++chunk) {
+        const int b = chunk & 1, use = chunk >> 1;
+        if (ok) ok = mbar_wait(acc_full(b), use & 1, abort_flag, err, 3);
+        ok = __all_sync(0xffffffffu, ok);
+        fence_after();
+        if (ok && mine) {
+          const uint32_t t0 = tmem + lane_off + 256u * b + 64u * ch;
+#pragma unroll
+          for (int h = 0; h < 8; ++h) {
+            float v0[8], v1[8];
+            tmem_ld2x8(t0 + 8 * h, t0 + 128 + 8 * h, v0, v1);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              float hi, lo;
+              two_sum(v0[i], v1[i], hi, lo);
+              float s, e;
+              two_sum(sh[8 * h + i], hi, s, e);
+              e += sl[8 * h + i] + lo;
+              sh[8 * h + i] = s + e;
+              sl[8 * h + i] = e - (sh[8 * h + i] - s);
+            }
+          }
         }
+        fence_before();
+        mbar_arrive(acc_empty(b));
+      }
+      // epilogue: this thread owns row `row`, columns n0 + 32 ch + i
+      const int gm = tl.m0 + row;
+      if (!mine || gm >= p.M) continue;
+      const int cbase = 64 * ch;
+      if (p.mode == 0) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          float hi, lo;
-          two_sum(v0[i], v1[i], hi, lo);
-          if (c > 0 && ok) {
+        for (int i = 0; i < 64; ++i) {
+          if (cbase + i >= Nt) break;
+          const int64_t o = int64_t(gm) * p.ldc + tl.n0 + cbase + i;
+          float hi = p.alpha * sh[i], lo = p.alpha * sl[i];
+          if (p.accumulate) {
             float s, e;
-            two_sum(sh[i], hi, s, e);
-            e += sl[i] + lo;
+            two_sum(p.Chi[o], hi, s, e);
+            e += p.Clo[o] + lo;
             hi = s + e;
             lo = e - (hi - s);
           }
-          sh[i] = hi;
-          sl[i] = lo;
+          p.Chi[o] = hi;
+          p.Clo[o] = lo;
         }
-        if (!last) {
-          if (ok) tmem_st2(lb + 256 + c0, lb + 384 + c0, sh, sl);
-          continue;
-        }
-        if (gm >= p.M) continue;
-        if (p.mode == 1 && c0 + 16 <= Nt) {
-          // 16 consecutive BF16 per plane: two 16-byte stores each (row starts and
-          // column offsets are multiples of 8 elements in every plane layout)
-          uint32_t h[8], m[8], l[8];
+      } else if (p.mode == 1 && cbase + 64 <= Nt) {
+        // 64 consecutive BF16 per plane as eight 16-byte stores (row starts and
+        // column offsets are multiples of 8 elements in every plane layout)
+        uint16_t* dst = p.Cp + int64_t(gm) * p.ldc + tl.n0 + cbase;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
+        for (int v = 0; v < 8; ++v) {
+          uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
             uint16_t hh[2], mm[2], ll[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-              const float a0 = p.alpha * sh[2 * i + u], a1 = p.alpha * sl[2 * i + u];
-              const __nv_bfloat16 bh = __float2bfloat16_rn(a0);
-              const float r = (a0 - __bfloat162float(bh)) + a1;
-              const __nv_bfloat16 bm = __float2bfloat16_rn(r);
-              const __nv_bfloat16 bl = __float2bfloat16_rn(r - __bfloat162float(bm));
-              hh[u] = bf_bits(bh);
-              mm[u] = bf_bits(bm);
-              ll[u] = bf_bits(bl);
+              const int c = 8 * v + 2 * i + u;
+              split3(p.alpha * sh[c], p.alpha * sl[c], hh[u], mm[u], ll[u]);
             }
-            h[i] = hh[0] | (uint32_t(hh[1]) << 16);
-            m[i] = mm[0] | (uint32_t(mm[1]) << 16);
-            l[i] = ll[0] | (uint32_t(ll[1]) << 16);
+            hw[i] = hh[0] | (uint32_t(hh[1]) << 16);
+            mw[i] = mm[0] | (uint32_t(mm[1]) << 16);
+            lw[i] = ll[0] | (uint32_t(ll[1]) << 16);
           }
-          uint16_t* dst = p.Cp + int64_t(gm) * p.ldc + tl.n0 + c0;
-          uint4* d0 = reinterpret_cast<uint4*>(dst);
-          uint4* d1 = reinterpret_cast<uint4*>(dst + p.psC);
-          uint4* d2 = reinterpret_cast<uint4*>(dst + 2 * p.psC);
-          d0[0] = make_uint4(h[0], h[1], h[2], h[3]);
-          d0[1] = make_uint4(h[4], h[5], h[6], h[7]);
-          d1[0] = make_uint4(m[0], m[1], m[2], m[3]);
-          d1[1] = make_uint4(m[4], m[5], m[6], m[7]);
-          d2[0] = make_uint4(l[0], l[1], l[2], l[3]);
-          d2[1] = make_uint4(l[4], l[5], l[6], l[7]);
-          continue;
+          reinterpret_cast<uint4*>(dst)[v] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          reinterpret_cast<uint4*>(dst + p.psC)[v] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+          reinterpret_cast<uint4*>(dst + 2 * p.psC)[v] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
+      } else {
+        // mode 1 tail, mode 2 (transposed store: tile column n goes to row n of C) or
+        // mode 3 (column n goes to the row of C given by its table entry)
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          if (c0 + i >= Nt) break;
-          const int64_t o = int64_t(gm) * p.ldc + tl.n0 + c0 + i;
-          if (p.mode == 0) {
-            float hi = p.alpha * sh[i], lo = p.alpha * sl[i];
-            if (p.accumulate) {
-              float s, e;
-              two_sum(p.Chi[o], hi, s, e);
-              e += p.Clo[o] + lo;
-              hi = s + e;
-              lo = e - (hi - s);
-            }
-            p.Chi[o] = hi;
-            p.Clo[o] = lo;
+        for (int i = 0; i < 64; ++i) {
+          if (cbase + i >= Nt) break;
+          const int n = tl.n0 + cbase + i;
+          int64_t o;
+          float al = p.alpha;
+          if (p.mode == 3) {
+            o = ccol[p.cm0 + n] + gm;
+            al = acol[p.cm0 + n];
           } else {
-            const float a0 = p.alpha * sh[i], a1 = p.alpha * sl[i];
-            const __nv_bfloat16 h = __float2bfloat16_rn(a0);
-            const float r = (a0 - __bfloat162float(h)) + a1;
-            const __nv_bfloat16 m = __float2bfloat16_rn(r);
-            const __nv_bfloat16 l = __float2bfloat16_rn(r - __bfloat162float(m));
-            p.Cp[o] = bf_bits(h);
-            p.Cp[o + p.psC] = bf_bits(m);
-            p.Cp[o + 2 * p.psC] = bf_bits(l);
+            o = (p.mode == 2) ? int64_t(n) * p.ldc + gm : int64_t(gm) * p.ldc + n;
           }
-        }
-      }
-      if (!last) {
-        fence_before();
-        mbar_arrive(drained);
-      }
-    }
-    if (nchunks == 0 && gm < p.M) {
-      // no contribution: C = 0 (or unchanged when accumulating)
-      for (int i = 0; i < Nt; ++i) {
-        const int64_t o = int64_t(gm) * p.ldc + tl.n0 + i;
-        if (p.mode == 0) {
-          if (!p.accumulate) {
-            p.Chi[o] = 0.f;
-            p.Clo[o] = 0.f;
-          }
-        } else {
-          p.Cp[o] = 0;
-          p.Cp[o + p.psC] = 0;
-          p.Cp[o + 2 * p.psC] = 0;
+          uint16_t h, m, l;
+          split3(al * sh[i], al * sl[i], h, m, l);
+          p.Cp[o] = h;
+          p.Cp[o + p.psC] = m;
+          p.Cp[o + 2 * p.psC] = l;
         }
       }
     }
@@ -487,14 +535,16 @@ __global__ void df_to_f64_kernel(const float* __restrict__ hi, const float* __re
 
 }  // namespace
 
-void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, const MixSeg* segs, int* err,
+void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, const MixSeg* segs,
+                       const int64_t* bcol, const int64_t* ccol, const float* acol, int* err, int nsm,
                        cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(mixed_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     attr = true;
   }
-  if (ntiles > 0) mixed_gemm_kernel<<<ntiles, NTHREADS, SMEM_BYTES, st>>>(tiles, probs, segs, err);
+  const int grid = ntiles < nsm ? ntiles : nsm;
+  if (ntiles > 0) mixed_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(tiles, ntiles, probs, segs, bcol, ccol, acol, err);
 }
 
 void launch_split(const SplitTask* t, int ntask, cudaStream_t st) {
