@@ -268,6 +268,8 @@ def main():
             "flops_per_sigma": flops, "operator_bytes": st["op_bytes"],
             "l2": "inputs larger than L2 (renormalised operators %.1f GB resident)" % (st["op_bytes"] / 1e9),
             "setup_s": round(t_setup, 1),
+            "plan": {k: st[k] for k in ("mix_tiles1", "mix_steps1", "mix_tiles2", "mix_steps2", "mix_x_elems",
+                                        "mix_plane_bytes", "gemm_problems", "gemm_segments")},
         },
         "clocks": clocks,
         "e2e": {"value": round(flops / e2e_s / 1e12, 4), "unit": "TFLOP/s",

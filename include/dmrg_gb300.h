@@ -166,10 +166,12 @@ dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedu
 dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi_dev, const double* lam_dev,
                                 double* g1_dev, double* g2_dev);
 
-/* Statistics of the prepared bond: int64[8] = psi_size, n_terms,
- * flops_stage1, flops_stage2, operator_bytes, gemm_problems, gemm_segments,
- * device kernel launches of one sigma. */
-dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out8);
+/* Statistics of the prepared bond: int64[16] = psi_size, n_terms,
+ * flops_stage1, flops_stage2 (algorithmic sigma flops), operator_bytes,
+ * gemm_problems, gemm_segments, kernel launches of one FP64 sigma, then for the
+ * split-BF16 plan: stage-1 tiles, stage-1 tile x K-stage count, stage-2 tiles,
+ * stage-2 tile x K-stage count, X elements, BF16 plane bytes, 0, 0. */
+dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out16);
 
 /* Kernel timing with CUDA events on the handle's stream (this library's
  * kernels only).  mode = 1: reset counters and start; mode = 0: stop and write

@@ -187,10 +187,11 @@ class Dmrg:
         return {c: {"ms": float(o[2 * i]), "launches": int(o[2 * i + 1])} for i, c in enumerate(PROFILE_CLASSES)}
 
     def stats(self):
-        o = np.zeros(8, dtype=np.int64)
+        o = np.zeros(16, dtype=np.int64)
         self._check(self.lib.dmrg_stats(self.h, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         keys = ["psi_size", "n_terms", "flops_stage1", "flops_stage2", "op_bytes", "gemm_problems",
-                "gemm_segments", "launches_per_sigma"]
+                "gemm_segments", "launches_per_sigma", "mix_tiles1", "mix_steps1", "mix_tiles2", "mix_steps2",
+                "mix_x_elems", "mix_plane_bytes"]
         return dict(zip(keys, (int(x) for x in o)))
 
 

@@ -304,6 +304,14 @@ dmrg_status dmrg_stats(dmrg_handle* h, int64_t* o) {
     o[5] = s.n_gemm_problems;
     o[6] = s.n_gemm_segments;
     o[7] = s.launches_per_sigma;
+    o[8] = s.mix_tiles1;
+    o[9] = s.mix_steps1;
+    o[10] = s.mix_tiles2;
+    o[11] = s.mix_steps2;
+    o[12] = s.mix_x_elems;
+    o[13] = s.mix_plane_bytes;
+    o[14] = 0;
+    o[15] = 0;
     return DMRG_OK;
   });
 }

@@ -125,6 +125,8 @@ struct BondStats {
   int64_t op_bytes = 0;   // algorithmic operator bytes read by one sigma (FP64)
   int n_gemm_problems = 0, n_gemm_segments = 0;
   int launches_per_sigma = 0;
+  // split-BF16 plan: tiles and K stages (32 wide) of stage 1 / stage 2, X elements, plane bytes
+  int64_t mix_tiles1 = 0, mix_steps1 = 0, mix_tiles2 = 0, mix_steps2 = 0, mix_x_elems = 0, mix_plane_bytes = 0;
 };
 
 class Engine {

@@ -535,7 +535,10 @@ void Engine::build_sigma_plan() {
       xmax_m = std::max(xmax_m, a);
     }
     xpl_ps_ = pad8(xmax_m) + 8;
+    st_.mix_x_elems = xmax_m;
+    st_.mix_plane_bytes = 6 * (opsL_ + opsR_ + opsLf_ + xpl_ps_ + psT_ps_ + psN_ps_ + psU_ps);
     xpl_ = static_cast<uint16_t*>(ex_->alloc(size_t(3 * xpl_ps_) * sizeof(uint16_t)));
+    ex_->zero(xpl_, size_t(3 * xpl_ps_) * sizeof(uint16_t));
     shi_ = static_cast<float*>(ex_->alloc(psi_n_ * sizeof(float)));
     slo_ = static_cast<float*>(ex_->alloc(psi_n_ * sizeof(float)));
     // split-K partial sums of stage 2 (double-float pairs), reduced in a fixed order
@@ -590,6 +593,9 @@ void Engine::build_sigma_plan() {
                                    float(t.c * sg)});
               continue;
             }
+            // rows with no contribution stay zero: the X buffer is cleared once when
+            // all terms fit one chunk, otherwise they are written as zero problems
+            if (fs.empty() && mranges.size() == 1) continue;
             MixProb q{};
             q.Cp = xpl_ + xoff + int64_t(EL.f_row[ft]) * cpj;
             q.psC = xpl_ps_;
@@ -696,6 +702,17 @@ void Engine::build_sigma_plan() {
           P2.push_back(q);
         }
       }
+      auto count = [&](const std::vector<MixProb>& PP, const std::vector<MixSeg>& SS, int64_t& tiles, int64_t& steps) {
+        for (const MixProb& q : PP) {
+          int64_t st = 0;
+          for (int k = q.s0; k < q.s1; ++k) st += (SS[k].K + 31) / 32;
+          const int64_t t = int64_t((q.M + 127) / 128) * ((q.N + 127) / 128);
+          tiles += t;
+          steps += t * st;
+        }
+      };
+      count(P1, S1, st_.mix_tiles1, st_.mix_steps1);
+      count(P2, S2, st_.mix_tiles2, st_.mix_steps2);
       Chunk ch;
       ch.plan1 = P1.empty() ? -1 : ex_->mix_plan_g(P1, S1, bcol, ccol, acol);
       ch.plan2 = ex_->mix_plan(P2, S2);

@@ -37,6 +37,7 @@ constexpr int PRODUCER_THREADS = 32 * PRODUCER_WARPS;
 constexpr int DRAIN_THREADS = 256;              // 8 warps: 4 lane quarters x 2 column halves
 constexpr int NTHREADS = 32 + PRODUCER_THREADS + DRAIN_THREADS;
 constexpr int CHUNK = 4;                        // K stages per accumulator chunk (128 K)
+constexpr int LAG = 2;                          // stages a producer keeps in flight before retiring one
 constexpr long long WAIT_CYCLES = 4000000000LL; // about 2 s at 2 GHz
 constexpr uint32_t TMEM_COLS = 512;
 
@@ -81,6 +82,16 @@ __device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag,
       }
     }
   }
+}
+
+// warp-level bounded wait: one lane polls the barrier, the other lanes wait at
+// the __syncwarp (so that hundreds of threads do not spin on shared memory)
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t a, uint32_t parity, volatile int* abort_flag, int* err,
+                                               int code) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(a, parity, abort_flag, err, code) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  return ok != 0;
 }
 
 // shared-memory matrix descriptor: canonical K-major layout without swizzle,
@@ -228,12 +239,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full(s), PRODUCER_THREADS);
+      mbar_init(full(s), PRODUCER_WARPS);
       mbar_init(empty(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full(b), 1);
-      mbar_init(acc_empty(b), DRAIN_THREADS);
+      mbar_init(acc_empty(b), DRAIN_THREADS / 32);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -326,7 +337,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int Kp = (g.K + 7) & ~7;
         for (int k0 = 0; k0 < g.K; k0 += BK, ++step) {
           const int st = step % STAGES;
-          if (step >= STAGES && !mbar_wait(empty(st), ((step / STAGES) - 1) & 1, abort_flag, err, 2)) {
+          if (step >= STAGES && !mbar_wait_warp(empty(st), ((step / STAGES) - 1) & 1, abort_flag, err, 2)) {
             stop = true;
             break;
           }
@@ -348,11 +359,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               cp_async16(base + (3 + q) * PLANE_BYTES + so, bb + q * g.psB, vb ? 16u : 0u);
             }
           }
-          // arrive on full(st) once all of this thread's copies have landed
-          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full(st)) : "memory");
+          // one commit group per stage; the stage issued LAG steps ago is retired when
+          // its group has landed: the warp syncs and one lane arrives on its full barrier
+          asm volatile("cp.async.commit_group;" ::: "memory");
+          if (step >= LAG) {
+            asm volatile("cp.async.wait_group %0;" ::"n"(LAG) : "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(full((step - LAG) % STAGES));
+          }
         }
       }
     }
+    // retire the last stages in order
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    if (lane == 0)
+      for (int r = (step > LAG ? step - LAG : 0); r < step; ++r) mbar_arrive(full(r % STAGES));
   } else {
     // ---- drain + epilogue
     const int dw = warp - 1 - PRODUCER_WARPS;   // 0..7
@@ -376,8 +398,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool mine = 64 * ch < Nmma;          // this warp's columns exist in the tile
       for (int c = 0; c < nch; ++c, ++chunk) {
         const int b = chunk & 1, use = chunk >> 1;
-        if (ok) ok = mbar_wait(acc_full(b), use & 1, abort_flag, err, 3);
-        ok = __all_sync(0xffffffffu, ok);
+        if (ok) ok = mbar_wait_warp(acc_full(b), use & 1, abort_flag, err, 3);
         fence_after();
         if (ok && mine) {
           const uint32_t t0 = tmem + lane_off + 256u * b + 64u * ch;
@@ -398,7 +419,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
         fence_before();
-        mbar_arrive(acc_empty(b));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty(b));
       }
       // epilogue: this thread owns row `row`, columns n0 + 32 ch + i
       const int gm = tl.m0 + row;
