@@ -204,15 +204,17 @@ class Engine {
   double* diag_ = nullptr;
   // split-BF16 tensor-core sigma
   bool mixed_ready_ = false;
-  uint16_t* oplL_ = nullptr;
-  uint16_t* oplR_ = nullptr;
-  uint16_t* oplLf_ = nullptr;   // fine (per sub-block) planes of the L' operators
+  // blocked split matrices (three BF16 planes each) and the element counts of
+  // their arenas
+  uint16_t* oplL_ = nullptr;    // H_L' on coarse blocks
+  uint16_t* oplR_ = nullptr;    // R' operators on coarse blocks, normal and transposed
+  uint16_t* oplLf_ = nullptr;   // L' operators per fine sub-block, normal and transposed
   int64_t opsL_ = 0, opsR_ = 0, opsLf_ = 0;
-  uint16_t* psiT_ = nullptr;
-  uint16_t* psiN_ = nullptr;
-  int64_t psT_ps_ = 0, psN_ps_ = 0;
-  uint16_t* xpl_ = nullptr;
-  int64_t xpl_ps_ = 0;
+  uint16_t* psiT_ = nullptr;    // psi^T per fine row block of L'
+  uint16_t* psiN_ = nullptr;    // psi and psi^T per coarse block (local terms)
+  int64_t psT_n_ = 0, psN_n_ = 0;
+  uint16_t* xpl_ = nullptr;     // stage-1 results X
+  int64_t xpl_n_ = 0;
   float* shi_ = nullptr;
   float* slo_ = nullptr;
   int psi_split_ = -1;

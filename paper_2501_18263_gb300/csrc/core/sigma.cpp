@@ -384,136 +384,164 @@ void Engine::build_sigma_plan() {
   // ---- split-BF16 tensor-core plans (precision 1): same terms and chunks as
   // above, evaluated on coarse (sector-level) blocks so that each stage is one
   // GEMM per block pair: stage 1 X{iT, jR} = O_L{iT <- iL} psi{iL, jR} with K =
-  // the padded rows of iL, stage 2 sigma{iT, jT} = sum_nu X_nu{iT, jR} O_R{jT <- jR}^T
+  // the rows of iL, stage 2 sigma{iT, jT} = sum_nu X_nu{iT, jR} O_R{jT <- jR}^T
   // with K concatenated over all terms.  Fine sub-blocks that are zero stay zero
-  // in the coarse planes.
+  // in the coarse operands.
+  //
+  // Every operand is a blocked split matrix (exec.h: rows padded to 8, K to 32,
+  // three BF16 planes interleaved per 8-row group and 32-wide K slab).  Along a
+  // coarse K dimension the fine sub-blocks start at multiples of 16 (rp / cp) and
+  // the total is padded to 32 (rowpad / colpad), so that the padding is zero.
   if (P_.precision != 0) {
     auto pad8 = [](int64_t x) { return (x + 7) & ~int64_t(7); };
+    auto pad16 = [](int64_t x) { return (x + 15) & ~int64_t(15); };
+    auto pad32 = [](int64_t x) { return (x + 31) & ~int64_t(31); };
+    auto bsize = [&](int64_t rows, int64_t kt) { return 3 * pad8(rows) * kt; };
     std::vector<int> rowpad(EL.coarse.q.size(), 0), colpad(ER.coarse.q.size(), 0);
     std::vector<int> rp(EL.f_dim.size(), 0), cp(ER.f_dim.size(), 0);
-    for (size_t i = 0; i < EL.coarse.q.size(); ++i)
+    for (size_t i = 0; i < EL.coarse.q.size(); ++i) {
       for (int f : EL.coarse_fines[i]) {
         rp[f] = rowpad[i];
-        rowpad[i] += int(pad8(EL.f_dim[f]));
+        rowpad[i] += int(pad16(EL.f_dim[f]));
       }
-    for (size_t j = 0; j < ER.coarse.q.size(); ++j)
+      rowpad[i] = int(pad32(rowpad[i]));
+    }
+    for (size_t j = 0; j < ER.coarse.q.size(); ++j) {
       for (int g : ER.coarse_fines[j]) {
         cp[g] = colpad[j];
-        colpad[j] += int(pad8(ER.f_dim[g]));
+        colpad[j] += int(pad16(ER.f_dim[g]));
       }
-    // coarse operator planes: normal N(a <- b) is dim(a) x pad(b); transposed
-    // T(a <- b) holds (O^T){b <- a} as dim(b) x pad(a)
+      colpad[j] = int(pad32(colpad[j]));
+    }
+    auto split_now = [&](const std::vector<SplitTask>& tk) {
+      int sp = ex_->split_plan(tk);
+      ex_->split_run(sp);
+      ex_->split_plan_free(sp);
+    };
+    auto arena = [&](int64_t n) {
+      uint16_t* a = static_cast<uint16_t*>(ex_->alloc(size_t(n + 64) * sizeof(uint16_t)));
+      ex_->zero(a, size_t(n + 64) * sizeof(uint16_t));
+      return a;
+    };
+    // coarse operator matrices: normal N(a <- b) is dim(a) rows x pad(b); transposed
+    // T(a <- b) holds (O^T){b <- a} as dim(b) rows x pad(a).  On L' only H_L' is
+    // used coarse (the local term); stage 1 reads the fine matrices below.
     using CKey = std::tuple<const Op*, int, int>;
     std::map<CKey, std::pair<int64_t, int64_t>> offL, offR;
-    auto planes = [&](const OpSet& os, const Enlarged& E, const std::vector<int>& pad, const std::vector<int>& pp,
-                      std::map<CKey, std::pair<int64_t, int64_t>>& off, uint16_t*& arena, int64_t& ps) {
+    auto coarse = [&](const OpSet& os, const Enlarged& E, const std::vector<int>& pad, const std::vector<int>& pp,
+                      const Op* only, std::map<CKey, std::pair<int64_t, int64_t>>& off, uint16_t*& ar,
+                      int64_t& n) {
       int64_t o = 0;
-      for (auto& kv : os.ops)
+      for (auto& kv : os.ops) {
+        if (only && &kv.second != only) continue;
         for (auto& bk : kv.second.blk) {
           const int ca = E.f_coarse[bk.r], cb = E.f_coarse[bk.c];
           CKey key{&kv.second, ca, cb};
           if (off.count(key)) continue;
           const int64_t on = o;
-          o += int64_t(E.coarse.dim[ca]) * pad[cb];
+          o += bsize(E.coarse.dim[ca], pad[cb]);
           const int64_t ot = o;
-          o += int64_t(E.coarse.dim[cb]) * pad[ca];
+          o += bsize(E.coarse.dim[cb], pad[ca]);
           off[key] = {on, ot};
         }
-      ps = pad8(o) + 8;
-      arena = static_cast<uint16_t*>(ex_->alloc(size_t(3 * ps) * sizeof(uint16_t)));
-      ex_->zero(arena, size_t(3 * ps) * sizeof(uint16_t));
+      }
+      n = o;
+      ar = arena(n);
       std::vector<SplitTask> tk;
-      for (auto& kv : os.ops)
+      for (auto& kv : os.ops) {
+        if (only && &kv.second != only) continue;
         for (auto& bk : kv.second.blk) {
           const int ca = E.f_coarse[bk.r], cb = E.f_coarse[bk.c];
           const auto& oo = off[CKey{&kv.second, ca, cb}];
-          tk.push_back(SplitTask{os.arena + bk.off, bk.rows, bk.cols, bk.cols, pad[cb], pad[ca], 0,
-                                 arena + oo.first + int64_t(E.f_row[bk.r]) * pad[cb] + pp[bk.c],
-                                 arena + oo.second + int64_t(E.f_row[bk.c]) * pad[ca] + pp[bk.r], ps});
+          tk.push_back(SplitTask{os.arena + bk.off, bk.rows, bk.cols, bk.cols, E.f_row[bk.r], pp[bk.c],
+                                 int(pad8(E.coarse.dim[ca])), pad[cb], E.f_row[bk.c], pp[bk.r],
+                                 int(pad8(E.coarse.dim[cb])), pad[ca], ar + oo.first, ar + oo.second});
         }
-      int sp = ex_->split_plan(tk);
-      ex_->split_run(sp);
-      ex_->split_plan_free(sp);
+      }
+      split_now(tk);
     };
-    planes(EopsL_, EL, rowpad, rp, offL, oplL_, opsL_);
-    planes(EopsR_, ER, colpad, cp, offR, oplR_, opsR_);
-    // fine planes of the L' operators for stage 1: every nonzero sub-block alone,
-    // normal (rows x pad8(cols)) and transposed (cols x pad8(rows))
+    coarse(EopsL_, EL, rowpad, rp, GL(OP_H, 0), offL, oplL_, opsL_);
+    coarse(EopsR_, ER, colpad, cp, nullptr, offR, oplR_, opsR_);
+    // fine matrices of the L' operators for stage 1: every nonzero sub-block alone,
+    // normal (rows x pad32(cols)) and transposed (cols x pad32(rows))
     {
       int64_t o = 0;
       for (auto& kv : EopsL_.ops)
         for (auto& bk : kv.second.blk) {
           bk.pn = o;
-          o += int64_t(bk.rows) * pad8(bk.cols);
+          o += bsize(bk.rows, pad32(bk.cols));
           bk.pt = o;
-          o += int64_t(bk.cols) * pad8(bk.rows);
+          o += bsize(bk.cols, pad32(bk.rows));
         }
-      opsLf_ = pad8(o) + 8;
-      oplLf_ = static_cast<uint16_t*>(ex_->alloc(size_t(3 * opsLf_) * sizeof(uint16_t)));
-      ex_->zero(oplLf_, size_t(3 * opsLf_) * sizeof(uint16_t));
+      opsLf_ = o;
+      oplLf_ = arena(o);
       std::vector<SplitTask> tk;
       for (auto& kv : EopsL_.ops)
         for (auto& bk : kv.second.blk)
-          tk.push_back(SplitTask{EopsL_.arena + bk.off, bk.rows, bk.cols, bk.cols, int(pad8(bk.cols)),
-                                 int(pad8(bk.rows)), 0, oplLf_ + bk.pn, oplLf_ + bk.pt, opsLf_});
-      int sp = ex_->split_plan(tk);
-      ex_->split_run(sp);
-      ex_->split_plan_free(sp);
+          tk.push_back(SplitTask{EopsL_.arena + bk.off, bk.rows, bk.cols, bk.cols, 0, 0, int(pad8(bk.rows)),
+                                 int(pad32(bk.cols)), 0, 0, int(pad8(bk.cols)), int(pad32(bk.rows)), oplLf_ + bk.pn,
+                                 oplLf_ + bk.pt});
+      split_now(tk);
     }
-    // psi planes: psiN (rows x colpad), psiT (colpad x rowpad), psiTu (cols x rowpad)
-    std::vector<int64_t> tOff(EL.coarse.q.size(), -1), nOff(EL.coarse.q.size(), -1), uOff(EL.coarse.q.size(), -1);
-    int64_t tT = 0, tN = 0, tU = 0;
+    // psi operands: psiT per fine row block f of L' (colpad(j) rows x pad32(dim f),
+    // the A operand of stage 1), psiN (dim(i) rows x colpad(j)) and psiU (dim(j)
+    // rows x rowpad(i)) per coarse block for the local terms
+    std::vector<int64_t> tOff(EL.f_dim.size(), -1), nOff(EL.coarse.q.size(), -1), uOff(EL.coarse.q.size(), -1);
+    int64_t tT = 0, tN = 0;
     for (size_t i = 0; i < EL.coarse.q.size(); ++i) {
       if (psi_off_[i] < 0) continue;
       const int j = psi_rcoarse_[i];
-      tOff[i] = tT;
-      tT += int64_t(colpad[j]) * rowpad[i];
+      for (int f : EL.coarse_fines[i]) {
+        tOff[f] = tT;
+        tT += bsize(colpad[j], pad32(EL.f_dim[f]));
+      }
       nOff[i] = tN;
-      tN += int64_t(EL.coarse.dim[i]) * colpad[j];
-      uOff[i] = tU;
-      tU += int64_t(ER.coarse.dim[j]) * rowpad[i];
+      tN += bsize(EL.coarse.dim[i], colpad[j]);
     }
-    psT_ps_ = pad8(tT) + 8;
-    psN_ps_ = pad8(tN) + 8;
-    const int64_t psU_ps = pad8(tU) + 8;
-    psiT_ = static_cast<uint16_t*>(ex_->alloc(size_t(3 * psT_ps_) * sizeof(uint16_t)));
-    psiN_ = static_cast<uint16_t*>(ex_->alloc(size_t(3 * (psN_ps_ + psU_ps)) * sizeof(uint16_t)));
-    uint16_t* psiU = psiN_ + 3 * psN_ps_;
-    ex_->zero(psiT_, size_t(3 * psT_ps_) * sizeof(uint16_t));
-    ex_->zero(psiN_, size_t(3 * (psN_ps_ + psU_ps)) * sizeof(uint16_t));
+    for (size_t i = 0; i < EL.coarse.q.size(); ++i) {
+      if (psi_off_[i] < 0) continue;
+      const int j = psi_rcoarse_[i];
+      uOff[i] = tN;
+      tN += bsize(ER.coarse.dim[j], rowpad[i]);
+    }
+    psT_n_ = tT;
+    psN_n_ = tN;
+    psiT_ = arena(tT);
+    psiN_ = arena(tN);
     {
       std::vector<SplitTask> tk;
       for (size_t i = 0; i < EL.coarse.q.size(); ++i) {
         if (psi_off_[i] < 0) continue;
         const int j = psi_rcoarse_[i];
         const int cols = ER.coarse.dim[j];
+        const int dl8 = int(pad8(EL.coarse.dim[i])), dr8 = int(pad8(ER.coarse.dim[j]));
         for (int f : EL.coarse_fines[i])
           for (int g : ER.coarse_fines[j]) {
             const double* src = psi_in_ + psi_off_[i] + int64_t(EL.f_row[f]) * cols + ER.f_row[g];
-            tk.push_back(SplitTask{src, EL.f_dim[f], ER.f_dim[g], cols, colpad[j], rowpad[i], 0,
-                                   psiN_ + nOff[i] + int64_t(EL.f_row[f]) * colpad[j] + cp[g], nullptr, psN_ps_});
-            tk.push_back(SplitTask{src, EL.f_dim[f], ER.f_dim[g], cols, colpad[j], rowpad[i], 0, nullptr,
-                                   psiT_ + tOff[i] + int64_t(cp[g]) * rowpad[i] + rp[f], psT_ps_});
-            tk.push_back(SplitTask{src, EL.f_dim[f], ER.f_dim[g], cols, colpad[j], rowpad[i], 0, nullptr,
-                                   psiU + uOff[i] + int64_t(ER.f_row[g]) * rowpad[i] + rp[f], psU_ps});
+            // psiN{i}: (f_row[f] + r, cp[g] + c); psiT{f}: (cp[g] + c, r);
+            // psiU{i}: (f_row[g] + c, rp[f] + r)
+            tk.push_back(SplitTask{src, EL.f_dim[f], ER.f_dim[g], cols, EL.f_row[f], cp[g], dl8, colpad[j],
+                                   ER.f_row[g], rp[f], dr8, rowpad[i], psiN_ + nOff[i], psiN_ + uOff[i]});
+            tk.push_back(SplitTask{src, EL.f_dim[f], ER.f_dim[g], cols, 0, 0, 0, 0, cp[g], 0, colpad[j],
+                                   int(pad32(EL.f_dim[f])), nullptr, psiT_ + tOff[f]});
           }
       }
       psi_split_ = ex_->split_plan(tk);
     }
-    // X planes per chunk: X{iT, jR} is rows(iT) x colpad(jR)
+    // X per chunk: X{iT, jR} is dim(iT) rows x colpad(jR)
     std::vector<std::vector<int64_t>> xmoff(T.size());
     std::vector<int64_t> xmsize(T.size(), 0);
     for (size_t n = 0; n < T.size(); ++n) {
       int64_t o = 0;
       for (const XBlk& xb : xl[n]) {
         xmoff[n].push_back(o);
-        o += int64_t(EL.coarse.dim[xb.iT]) * colpad[xb.jR];
+        o += bsize(EL.coarse.dim[xb.iT], colpad[xb.jR]);
       }
       xmsize[n] = o;
     }
-    // one X buffer for all terms unless it exceeds the cap (3 BF16 planes per element)
-    const int64_t xcap_m = P_.mem_cap ? std::max<int64_t>(int64_t(1) << 24, int64_t(P_.mem_cap / 2 / 6))
-                                      : int64_t(1) << 33;
+    // one X buffer for all terms unless it exceeds the cap (2 bytes per element)
+    const int64_t xcap_m = P_.mem_cap ? std::max<int64_t>(int64_t(3) << 24, int64_t(P_.mem_cap / 4))
+                                      : int64_t(3) << 33;
     std::vector<std::pair<size_t, size_t>> mranges;
     {
       size_t st0 = 0;
@@ -534,16 +562,17 @@ void Engine::build_sigma_plan() {
       for (size_t n = rg.first; n < rg.second; ++n) a += xmsize[n];
       xmax_m = std::max(xmax_m, a);
     }
-    xpl_ps_ = pad8(xmax_m) + 8;
-    st_.mix_x_elems = xmax_m;
-    st_.mix_plane_bytes = 6 * (opsL_ + opsR_ + opsLf_ + xpl_ps_ + psT_ps_ + psN_ps_ + psU_ps);
-    xpl_ = static_cast<uint16_t*>(ex_->alloc(size_t(3 * xpl_ps_) * sizeof(uint16_t)));
-    ex_->zero(xpl_, size_t(3 * xpl_ps_) * sizeof(uint16_t));
+    xpl_n_ = xmax_m;
+    st_.mix_x_elems = xmax_m / 3;
+    st_.mix_plane_bytes = 2 * (opsL_ + opsR_ + opsLf_ + xpl_n_ + psT_n_ + psN_n_);
+    xpl_ = arena(xpl_n_);
     shi_ = static_cast<float*>(ex_->alloc(psi_n_ * sizeof(float)));
     slo_ = static_cast<float*>(ex_->alloc(psi_n_ * sizeof(float)));
-    // split-K partial sums of stage 2 (double-float pairs), reduced in a fixed order
+    // split-K partial sums of stage 2 (double-float pairs), reduced in a fixed
+    // order, and one more slot for the local term H_L' (x) 1
     const int kMaxParts = 16;
-    part_ = static_cast<float*>(ex_->alloc(size_t(kMaxParts) * 2 * psi_n_ * sizeof(float)));
+    part_ = static_cast<float*>(ex_->alloc(size_t(kMaxParts + 1) * 2 * psi_n_ * sizeof(float)));
+    ex_->zero(part_, size_t(kMaxParts + 1) * 2 * psi_n_ * sizeof(float));
     nparts_ = 1;
     for (size_t ci = 0; ci < mranges.size(); ++ci) {
       const size_t n0 = mranges[ci].first, n1 = mranges[ci].second;
@@ -555,19 +584,21 @@ void Engine::build_sigma_plan() {
           a += xmsize[n];
         }
       }
-      // Stage 1 on nonzero fine sub-blocks, as transposed tiles (tile rows run over
-      // the padded R' columns of X, tile columns over rows of X).  A row block ft of
-      // X_nu that receives a single fine block (ft <- f) -- every normal operator,
-      // by its Kronecker form -- joins the gathered problem of (psi block, f): all
-      // such rows of all terms share the A operand psi^T{jR, f} and become columns
-      // of one wide GEMM (B rows and output rows from per-column tables).  Rows
-      // with several contributing f (complementary S_q) are separate problems.
+      // Stage 1 on nonzero fine sub-blocks: tile rows run over rows of X, tile
+      // columns over its padded R' columns.  A row block ft of X_nu that receives a
+      // single fine block (ft <- f) -- every normal operator, by its Kronecker form
+      // -- joins the gathered problem of (psi block, f): all such rows of all terms
+      // share the B operand psi^T{jR, f} and become rows of one tall GEMM (A rows
+      // and output rows from per-row tables).  Rows with several contributing f
+      // (complementary S_q) are separate problems.
       std::vector<MixProb> P1;
       std::vector<MixSeg> S1;
       std::vector<int64_t> bcol, ccol;
       std::vector<float> acol;
-      struct GCol { int64_t b, c; float a; };
-      std::map<std::tuple<int, int, int>, std::vector<GCol>> groups;   // (iL, jR, f) -> columns
+      // rows come in units of 8 (one 8-row group of a fine operator matrix: its
+      // offset and K-slab stride); c < 0 marks a padding row past the last one
+      struct GUnit { int64_t b, bs; int64_t c[8]; float a; };
+      std::map<std::tuple<int, int, int>, std::vector<GUnit>> groups;   // (iL, jR, f) -> row units
       for (size_t n = n0; n < n1; ++n) {
         const Term& t = T[n];
         if (!t.L) continue;
@@ -576,6 +607,7 @@ void Engine::build_sigma_plan() {
           const QN qL = EL.coarse.q[xb.iL];
           const double sg = (t.R && t.R->odd && (qL.n() & 1)) ? -1.0 : 1.0;
           const int cpj = colpad[xb.jR];
+          const int xr8 = int(pad8(EL.coarse.dim[xb.iT]));
           const int64_t xoff = xb0[n] + xmoff[n][k];
           for (int ft : EL.coarse_fines[xb.iT]) {
             std::vector<std::pair<int, const OpBlk*>> fs;
@@ -587,31 +619,43 @@ void Engine::build_sigma_plan() {
               const int f = fs[0].first;
               const OpBlk* ob = fs[0].second;
               const int64_t b0 = t.Lt ? ob->pt : ob->pn;
+              const int64_t kt = pad32(EL.f_dim[f]);
+              const int br8 = int(pad8(EL.f_dim[ft]));   // rows of the fine matrix
               auto& col = groups[std::make_tuple(xb.iL, xb.jR, f)];
-              for (int j = 0; j < EL.f_dim[ft]; ++j)
-                col.push_back(GCol{b0 + int64_t(j) * pad8(EL.f_dim[f]), xoff + int64_t(EL.f_row[ft] + j) * cpj,
-                                   float(t.c * sg)});
+              for (int j8 = 0; j8 < EL.f_dim[ft]; j8 += 8) {
+                const int rb = j8 >> 7, hb = std::min(128, br8 - 128 * rb);
+                GUnit u{b0 + int64_t(rb) * 384 * kt + ((j8 & 127) >> 3) * 768, int64_t(96) * hb, {},
+                        float(t.c * sg)};
+                for (int e = 0; e < 8; ++e) {
+                  const int r = EL.f_row[ft] + j8 + e, xrb = r >> 7, rr = r & 127;
+                  const int hx = std::min(128, xr8 - 128 * xrb);
+                  u.c[e] = (j8 + e < EL.f_dim[ft])
+                               ? ((xoff + int64_t(xrb) * 384 * cpj + (rr >> 3) * 768 + (rr & 7) * 8) |
+                                  (int64_t(hx >> 3) << 48))
+                               : -1;
+                }
+                col.push_back(u);
+              }
               continue;
             }
             // rows with no contribution stay zero: the X buffer is cleared once when
             // all terms fit one chunk, otherwise they are written as zero problems
             if (fs.empty() && mranges.size() == 1) continue;
             MixProb q{};
-            q.Cp = xpl_ + xoff + int64_t(EL.f_row[ft]) * cpj;
-            q.psC = xpl_ps_;
+            q.Cp = xpl_ + xoff;
+            q.row0 = EL.f_row[ft];
+            q.crows = xr8;
             q.ldc = cpj;
-            q.M = cpj;
-            q.N = EL.f_dim[ft];
+            q.M = EL.f_dim[ft];
+            q.N = cpj;
             q.alpha = float(t.c * sg);
             q.mode = 2;
-            q.accumulate = 0;
             q.cm0 = -1;
             q.s0 = int(S1.size());
             for (auto& fb : fs) {
               const int f = fb.first;
-              const uint16_t* Bp = oplLf_ + (t.Lt ? fb.second->pt : fb.second->pn);
-              S1.push_back(MixSeg{psiT_ + tOff[xb.iL] + rp[f], Bp, psT_ps_, opsLf_, rowpad[xb.iL],
-                                  int(pad8(EL.f_dim[f])), EL.f_dim[f], 0});
+              const uint16_t* Ap = oplLf_ + (t.Lt ? fb.second->pt : fb.second->pn);
+              S1.push_back(MixSeg{Ap, psiT_ + tOff[f], EL.f_dim[f], 0});
             }
             q.s1 = int(S1.size());
             P1.push_back(q);
@@ -619,24 +663,25 @@ void Engine::build_sigma_plan() {
         }
       }
       for (auto& gk : groups) {
-        const int iL = std::get<0>(gk.first), jR = std::get<1>(gk.first), f = std::get<2>(gk.first);
+        const int jR = std::get<1>(gk.first), f = std::get<2>(gk.first);
         MixProb q{};
         q.Cp = xpl_;
-        q.psC = xpl_ps_;
         q.ldc = colpad[jR];
-        q.M = colpad[jR];
-        q.N = int(gk.second.size());
+        q.M = 8 * int(gk.second.size());
+        q.N = colpad[jR];
         q.alpha = 1.0f;
         q.mode = 3;
-        q.accumulate = 0;
-        q.cm0 = int64_t(bcol.size());
-        for (const GCol& c : gk.second) {
-          bcol.push_back(c.b);
-          ccol.push_back(c.c);
-          acol.push_back(c.a);
+        q.cm0 = int64_t(ccol.size());
+        for (const GUnit& u : gk.second) {
+          bcol.push_back(u.b);
+          bcol.push_back(u.bs);
+          for (int e = 0; e < 8; ++e) {
+            ccol.push_back(u.c[e]);
+            acol.push_back(u.a);
+          }
         }
         q.s0 = int(S1.size());
-        S1.push_back(MixSeg{psiT_ + tOff[iL] + rp[f], oplLf_, psT_ps_, opsLf_, rowpad[iL], 8, EL.f_dim[f], 0});
+        S1.push_back(MixSeg{oplLf_, psiT_ + tOff[f], EL.f_dim[f], 0});
         q.s1 = int(S1.size());
         P1.push_back(q);
       }
@@ -660,11 +705,11 @@ void Engine::build_sigma_plan() {
           const uint16_t* B = oplR_ + (t.Rt ? it->second.second : it->second.first);
           if (!t.L) {
             if (jR != jT) continue;
-            bk.segs.push_back(MixSeg{psiN_ + nOff[iT], B, psN_ps_, opsR_, colpad[jT], colpad[jT], colpad[jT], 0});
+            bk.segs.push_back(MixSeg{psiN_ + nOff[iT], B, colpad[jT], 0});
           } else {
             const int xi = xidx[n][iT];
             if (xi < 0 || xl[n][xi].jR != jR) continue;
-            bk.segs.push_back(MixSeg{xpl_ + xb0[n] + xmoff[n][xi], B, xpl_ps_, opsR_, colpad[jR], colpad[jR], colpad[jR], 0});
+            bk.segs.push_back(MixSeg{xpl_ + xb0[n] + xmoff[n][xi], B, colpad[jR], 0});
           }
           bk.K += colpad[jR];
         }
@@ -692,7 +737,6 @@ void Engine::build_sigma_plan() {
           q.N = ER.coarse.dim[bk.jT];
           q.alpha = 1.0f;
           q.mode = 0;
-          q.accumulate = 0;
           q.s0 = int(S2.size());
           while (sidx < bk.segs.size() && (done < goal || pp == parts - 1)) {
             done += bk.segs[sidx].K;
@@ -727,17 +771,18 @@ void Engine::build_sigma_plan() {
         const int j = psi_rcoarse_[i];
         auto it = offL.find(CKey{HL, int(i), int(i)});
         if (it == offL.end()) continue;
+        // written into the extra part slot (never cleared: the same blocks are
+        // rewritten by every call and the others stay zero)
         MixProb q{};
-        q.Chi = shi_ + psi_off_[i];
-        q.Clo = slo_ + psi_off_[i];
+        q.Chi = part_ + int64_t(nparts_) * 2 * psi_n_ + psi_off_[i];
+        q.Clo = q.Chi + psi_n_;
         q.ldc = ER.coarse.dim[j];
         q.M = EL.coarse.dim[i];
         q.N = ER.coarse.dim[j];
         q.alpha = 1.0f;
         q.mode = 0;
-        q.accumulate = 1;
         q.s0 = int(S3.size());
-        S3.push_back(MixSeg{oplL_ + it->second.first, psiU + uOff[i], opsL_, psU_ps, rowpad[i], rowpad[i], rowpad[i], 0});
+        S3.push_back(MixSeg{oplL_ + it->second.first, psiN_ + uOff[i], rowpad[i], 0});
         q.s1 = int(S3.size());
         P3.push_back(q);
       }
@@ -843,13 +888,14 @@ void Engine::sigma_precision(const double* psi, double* sig, int precision) {
   }
   ex_->d2d(psi_in_, psi, psi_n_ * sizeof(double));
   ex_->split_run(psi_split_);
+  // H_L' (x) 1 goes to part slot nparts_, summed with the first chunk's parts
+  if (mplan_hl_ >= 0) ex_->mix_run(mplan_hl_);
   for (size_t c = 0; c < mchunks_.size(); ++c) {
     if (mchunks_[c].plan1 >= 0) ex_->mix_run(mchunks_[c].plan1);
     ex_->zero(part_, size_t(nparts_) * 2 * psi_n_ * sizeof(float));
     ex_->mix_run(mchunks_[c].plan2);
-    ex_->reduce_parts(part_, nparts_, psi_n_, shi_, slo_, c > 0);
+    ex_->reduce_parts(part_, nparts_ + (c == 0 ? 1 : 0), psi_n_, shi_, slo_, c > 0);
   }
-  if (mplan_hl_ >= 0) ex_->mix_run(mplan_hl_);
   ex_->df_to_f64(shi_, slo_, sig, psi_n_);
 }
 

@@ -48,40 +48,67 @@ struct DiagTask {
 };
 
 // ---- split-BF16 tensor-core path -------------------------------------------
-// Operands are stored as three BF16 planes (x ~ hi + mid + lo), plane p of an
-// operand at ptr + p * plane_stride.  Every operand is K-major: row r holds K
-// contiguous elements at ptr + r * ld; rows start on 16-byte boundaries (ld and
-// plane strides multiples of 8 elements) and the elements between K and
-// round8(K) are zero.
+// An operand x is carried as three BF16 planes (x ~ hi + mid + lo) stored
+// together in a "blocked split matrix": for a matrix with R rows (R8 = R padded
+// to 8) and K extent Kt (a multiple of 32), rows form blocks of 128 (the last
+// one h = min(128, R8 - 128 rb) rows), each block is cut into K slabs of 32, and
+// one slab holds, per 8-row group, the three planes' 8 x 32 pieces as 8 x 8 core
+// matrices (8 rows x 16 bytes).  Element (plane q, row r, k) is at
+//     rb * 384 Kt + (k / 32) * 96 h + (rr / 8) * 768 + q * 256
+//       + ((k % 32) / 8) * 64 + (rr % 8) * 8 + k % 8,      rb = r / 128, rr = r % 128
+// so the piece of a 128-row tile that one 32-wide K step needs (all three planes)
+// is one contiguous run of 192 h bytes.  Padding rows and columns are zero.
+#if defined(__CUDACC__)
+#define DMRG_HD __host__ __device__
+#else
+#define DMRG_HD
+#endif
+DMRG_HD inline int64_t blk_off(int q, int r, int k, int R8, int Kt) {
+  const int rb = r >> 7, rr = r & 127;
+  const int h = (R8 - (rb << 7)) < 128 ? (R8 - (rb << 7)) : 128;
+  return int64_t(rb) * 384 * Kt + int64_t(k >> 5) * 96 * h + (rr >> 3) * 768 + q * 256 + ((k & 31) >> 3) * 64 +
+         (rr & 7) * 8 + (k & 7);
+}
+DMRG_HD inline int64_t blk_size(int R, int Kt) { return int64_t(3) * ((R + 7) & ~7) * Kt; }
+
+// one K segment: A (M rows) and B (N rows) are blocked split matrices with the
+// same K extent pad32(K); the MMA runs over k < K (elements past K are zero)
 struct MixSeg {
-  const uint16_t* A;   // M rows (tile rows) x K
-  const uint16_t* B;   // N rows (tile cols) x K
-  int64_t psA, psB;
-  int lda, ldb, K, pad;
+  const uint16_t* A;
+  const uint16_t* B;
+  int K, pad;
 };
 // C (M x N) = alpha * sum_seg A_seg B_seg^T
-//   mode 0: C kept as a float pair (hi, lo) at Chi/Clo (+= if accumulate)
-//   mode 1: C written as three BF16 planes at Cp (plane stride psC)
-//   mode 2: as mode 1 but transposed: tile column n is written to row n of C
-//   mode 3: gathered columns: column n takes its B row at B + bcol[cm0 + n] and is
-//           written (transposed, scaled by acol[cm0 + n]) to Cp + ccol[cm0 + n]
+//   mode 0: C stored as a float pair (hi, lo), row-major with ld = ldc, at Chi/Clo
+//   mode 2: C is a blocked split matrix (R8 = crows, Kt = ldc) at Cp; tile row m
+//           is its row row0 + m, tile column n its column n (N a multiple of 32)
+//   mode 3: gathered rows (cm0 and M multiples of 8): the 8-row group g of A (one
+//           8-row group of some blocked split matrix) is at A + bcol[2 u] +
+//           s * bcol[2 u + 1] for K slab s, u = cm0 / 8 + g; row m is written,
+//           scaled by acol[cm0 + m], into the row of the blocked split matrix C
+//           whose row part (the terms of blk_off that depend on r) is
+//           ccol[cm0 + m] & (2^48 - 1) and whose row block holds
+//           8 * (ccol[cm0 + m] >> 48) rows (ccol < 0: padding, not stored)
 struct MixProb {
   float* Chi;
   float* Clo;
   uint16_t* Cp;
-  int64_t psC;
   int ldc, M, N, s0, s1;
   float alpha;
-  int mode, accumulate;
+  int mode, pad;
   int64_t cm0;
+  int row0, crows;
 };
-// FP64 block (rows x cols, ld) -> BF16 planes, normal (rows x ldn) and/or transposed (cols x ldt)
+// FP64 block (rows x cols, ld) -> blocked split matrices: element (r, c) goes to
+// (rn0 + r, cn0 + c) of the matrix at dn (rn8 padded rows, K extent ktn) and/or
+// to (rt0 + c, ct0 + r) of the matrix at dt (transposed copy)
 struct SplitTask {
   const double* src;
-  int rows, cols, ld, ldn, ldt, pad;
+  int rows, cols, ld;
+  int rn0, cn0, rn8, ktn;
+  int rt0, ct0, rt8, ktt;
   uint16_t* dn;
   uint16_t* dt;
-  int64_t ps;
 };
 
 class Exec {

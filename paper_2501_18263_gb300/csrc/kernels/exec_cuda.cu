@@ -609,9 +609,24 @@ class CudaExec : public Exec {
   int mix_plan_g(const std::vector<MixProb>& p, const std::vector<MixSeg>& s, const std::vector<int64_t>& bcol,
                  const std::vector<int64_t>& ccol, const std::vector<float>& acol) override {
     for (const MixSeg& g : s) {
-      if ((reinterpret_cast<uintptr_t>(g.A) & 15) || (reinterpret_cast<uintptr_t>(g.B) & 15) || (g.lda & 7) ||
-          (g.ldb & 7) || (g.psA & 7) || (g.psB & 7) || g.K <= 0)
-        throw std::runtime_error("mix_plan: operand not 16-byte aligned / padded");
+      // blocked split matrices are built of 128-byte core-matrix pairs: every
+      // bulk copy source is 16-byte aligned when the matrix base is
+      if ((reinterpret_cast<uintptr_t>(g.A) & 15) || (reinterpret_cast<uintptr_t>(g.B) & 15) || g.K <= 0)
+        throw std::runtime_error("mix_plan: operand not 16-byte aligned");
+    }
+    for (const MixProb& q : p) {
+      if (q.mode < 0 || q.mode > 3 || q.mode == 1 || q.M <= 0 || q.N < 0 || q.s0 < 0 || q.s1 > int(s.size()) ||
+          q.s0 > q.s1)
+        throw std::runtime_error("mix_plan: bad problem");
+      if (q.mode >= 2 && ((q.ldc & 31) || (q.N & 31) || q.N > q.ldc))
+        throw std::runtime_error("mix_plan: bad split-matrix output");
+      if (q.mode == 2 && (q.row0 < 0 || q.row0 + q.M > q.crows || (q.crows & 7)))
+        throw std::runtime_error("mix_plan: bad dense-row problem");
+      if (q.mode == 3 && ((q.cm0 & 7) || (q.M & 7) || q.cm0 < 0 || q.cm0 + q.M > int64_t(ccol.size()) ||
+                          q.cm0 + q.M > int64_t(acol.size()) || (q.cm0 + q.M) / 4 > int64_t(bcol.size())))
+        throw std::runtime_error("mix_plan: bad gathered problem");
+      for (int k = q.s0; k < q.s1; ++k)
+        if (s[k].A == nullptr || s[k].B == nullptr) throw std::runtime_error("mix_plan: bad segment");
     }
     std::vector<MixTile> tiles;
     std::vector<int64_t> work;
@@ -620,7 +635,7 @@ class CudaExec : public Exec {
       for (int q = p[i].s0; q < p[i].s1; ++q) w += (s[q].K + 31) / 32;
       for (int m0 = 0; m0 < p[i].M; m0 += MIX_TM)
         for (int n0 = 0; n0 < p[i].N; n0 += MIX_TN) {
-          tiles.push_back(MixTile{int(i), m0, n0, 0});
+          tiles.push_back(MixTile{int(i), m0, n0, int(w - 1)});
           work.push_back(w);
         }
     }

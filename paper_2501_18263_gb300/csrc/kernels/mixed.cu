@@ -8,14 +8,16 @@
 // 2^8 smaller than the result.  Every product of two BF16 values is exact in
 // FP32, but the tensor core's FP32 accumulation loses about a third of an ulp
 // per K = 16 step, so the accumulators only ever hold one chunk of K (CHUNK
-// stages): after each chunk they are drained into a double-float running sum
-// (hi + lo, TwoSum) kept in TMEM columns [256, 512).
+// stages): after each chunk the drain warps fold them into a double-float
+// running sum (hi + lo, TwoSum) held in registers.
 //
-// CTA = 9 warps.  Warp 0 allocates TMEM and one elected lane issues the MMAs;
-// warps 1-4 load operand tiles (16-byte vector loads into the canonical
-// no-swizzle K-major core-matrix layout); warps 5-8 drain the accumulators and
-// run the epilogue.  A ring of four shared-memory stages is guarded by
-// mbarriers; every wait is bounded and sets an error word instead of hanging.
+// Every operand plane lives in HBM in the tensor core's core-matrix tiling (8
+// rows x 16 bytes per core matrix, the K groups of an 8-row group contiguous), so
+// the slice of one plane that a stage needs is one contiguous run of at most 512
+// bytes per 8-row group, moved by cp.async.bulk straight into the canonical
+// no-swizzle K-major shared-memory layout.  A ring of four stages is guarded by
+// mbarriers (the full barriers count the copies' bytes); every wait is bounded
+// and sets an error word instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -26,22 +28,46 @@
 namespace dmrg {
 namespace {
 
-constexpr int BK = 32;                          // K elements per stage
+constexpr int BK = 32;                          // K elements per stage (one K slab)
 constexpr int STAGES = 4;
-constexpr int PLANE_BYTES = MIX_TM * BK * 2;    // one 128 x 32 BF16 plane: 8 KiB
-constexpr int STAGE_BYTES = 6 * PLANE_BYTES;    // 3 A planes + 3 B planes
+constexpr int RG_BYTES = 3 * 8 * BK * 2;        // one 8-row group of a slab, three planes: 1536 B
+constexpr int OPER_BYTES = 16 * RG_BYTES;       // a 128-row operand slab: 24 KiB
+constexpr int STAGE_BYTES = 2 * OPER_BYTES;     // A and B
 constexpr int BAR_BYTES = 256;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES;
-constexpr int PRODUCER_WARPS = 3;
-constexpr int PRODUCER_THREADS = 32 * PRODUCER_WARPS;
-constexpr int DRAIN_THREADS = 256;              // 8 warps: 4 lane quarters x 2 column halves
-constexpr int NTHREADS = 32 + PRODUCER_THREADS + DRAIN_THREADS;
+constexpr int DRAIN_THREADS = 512;              // 16 warps: 4 lane quarters x 4 column quarters
+constexpr int DRAIN_COLS = 32;                  // accumulator columns per drain thread
+constexpr int NTHREADS = 32 + 32 + DRAIN_THREADS;
 constexpr int CHUNK = 4;                        // K stages per accumulator chunk (128 K)
-constexpr int LAG = 2;                          // stages a producer keeps in flight before retiring one
 constexpr long long WAIT_CYCLES = 4000000000LL; // about 2 s at 2 GHz
 constexpr uint32_t TMEM_COLS = 512;
 
-static_assert(MIX_TN == MIX_TM, "B tile uses the A plane size");
+static_assert(MIX_TN == MIX_TM && MIX_TM == 128, "tiles are 128 x 128");
+
+// control word of a ring stage, written by the producer beside the stage's data
+struct StageInfo {
+  int ksub;   // K = 16 MMA steps in the stage (1 or 2); 0: no more stages
+  int last;   // last stage of its tile
+  int nmma;   // MMA N of the tile
+  int pad;
+};
+// per-tile record handed from the producer to the drain warps (double-buffered)
+struct alignas(16) TileSlot {
+  int64_t c[MIX_TM];   // mode 3: output-row table entries of the tile's rows
+  float a[MIX_TM];     // mode 3: row scales
+  float* Chi;
+  float* Clo;
+  uint16_t* Cp;
+  int m0, n0, Nt, nch;
+  int M, ldc, mode, pad0;
+  int row0, crows;
+  float alpha;
+  int pad;
+};
+constexpr int SLOT_OFF = STAGES * STAGE_BYTES;
+constexpr int INFO_OFF = SLOT_OFF + 2 * static_cast<int>(sizeof(TileSlot));
+constexpr int BAR_OFF = INFO_OFF + STAGES * static_cast<int>(sizeof(StageInfo));
+constexpr int SMEM_BYTES = BAR_OFF + BAR_BYTES;
+static_assert(sizeof(TileSlot) % 16 == 0 && SMEM_BYTES <= 232448, "shared memory layout");
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -84,6 +110,18 @@ __device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag,
   }
 }
 
+// wait bounded by time alone (used on the way out, after an abort, for the
+// kernel's own asynchronous copies and MMAs still in flight)
+__device__ void mbar_wait_exit(uint32_t a, uint32_t parity, int* err) {
+  const long long t0 = clock64();
+  while (!mbar_try(a, parity)) {
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicExch(err, 5);
+      return;
+    }
+  }
+}
+
 // warp-level bounded wait: one lane polls the barrier, the other lanes wait at
 // the __syncwarp (so that hundreds of threads do not spin on shared memory)
 __device__ __forceinline__ bool mbar_wait_warp(uint32_t a, uint32_t parity, volatile int* abort_flag, int* err,
@@ -96,12 +134,13 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t a, uint32_t parity, vola
 
 // shared-memory matrix descriptor: canonical K-major layout without swizzle,
 // core matrices of 8 rows x 16 bytes; LBO = 128 B (next core matrix along K),
-// SBO = 512 B (next 8-row group along M/N, BK/8 core matrices per group)
+// SBO = 1536 B (next 8-row group along M/N: the three planes of a group are
+// interleaved, plane q at +512 q)
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
   d |= static_cast<uint64_t>((128u >> 4) & 0x3FFFu) << 16;
-  d |= static_cast<uint64_t>(((BK / 8) * 128u >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>((static_cast<uint32_t>(RG_BYTES) >> 4) & 0x3FFFu) << 32;
   d |= static_cast<uint64_t>(1) << 46;  // descriptor version of the 5th-generation tensor core
   return d;
 }
@@ -129,46 +168,16 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// two 32-lane x 16-column loads (acc0 and acc1 chunks) and the wait, in one statement
-__device__ __forceinline__ void tmem_ld2(uint32_t t0, uint32_t t1, float* v0, float* v1) {
-  uint32_t a[16], b[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
-        "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]),
-        "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]),
-        "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15])
-      : "r"(t0), "r"(t1)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    v0[i] = __uint_as_float(a[i]);
-    v1[i] = __uint_as_float(b[i]);
-  }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void tmem_st2(uint32_t t0, uint32_t t1, const float* v0, const float* v1) {
-  uint32_t a[16], b[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    a[i] = __float_as_uint(v0[i]);
-    b[i] = __float_as_uint(v1[i]);
-  }
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%32], {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15};\n\t"
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%33], {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31};\n\t"
-      "tcgen05.wait::st.sync.aligned;\n" ::"r"(a[0]),
-      "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[8]), "r"(a[9]),
-      "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), "r"(a[15]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
-      "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]),
-      "r"(b[12]), "r"(b[13]), "r"(b[14]), "r"(b[15]), "r"(t0), "r"(t1)
-      : "memory");
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+// global -> shared bulk copy (16-byte aligned, multiple of 16 bytes), completion
+// counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 __device__ __forceinline__ uint16_t bf_bits(__nv_bfloat16 x) { return __bfloat16_as_ushort(x); }
@@ -210,24 +219,26 @@ __device__ __forceinline__ void tmem_ld2x8(uint32_t t0, uint32_t t1, float* v0, 
 }
 
 // Persistent split-BF16 grouped GEMM.  Grid = min(#tiles, #SMs); CTA c takes the
-// tiles c, c + G, c + 2G, ... of a list sorted by decreasing work.  12 warps
-// (three per SM sub-partition, so up to 168 registers each):
+// tiles c, c + G, c + 2G, ... of a list sorted by decreasing work.  18 warps (at
+// most five per SM sub-partition, so 96 registers each):
 //   warp 0        TMEM allocation and the MMA issuer (one lane)
-//   warps 1-3     producers: 16-byte loads of A/B planes into the smem ring
-//   warps 4-11    drain + epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and
-//                 columns 64 ((w - 4) / 4) .. +63 of each accumulator chunk
+//   warp 1        producer: plan records, tile slots and bulk copies into the ring
+//   warps 2-17    drain + epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and
+//                 columns 32 ((w - 2) / 4) .. +31 of each accumulator chunk
 // The accumulators are double-buffered per chunk of CHUNK stages: buffer b holds
 // acc0 (hi x hi) in TMEM columns [256 b, 256 b + 128) and acc1 (the five small
 // products) in [256 b + 128, 256 b + 256); while the drain warps fold chunk g
 // into their double-float register sums the MMA warp fills the other buffer.
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __maxnreg__(96)
     mixed_gemm_kernel(const MixTile* __restrict__ tiles, int ntiles, const MixProb* __restrict__ probs,
                       const MixSeg* __restrict__ segs, const int64_t* __restrict__ bcol,
                       const int64_t* __restrict__ ccol, const float* __restrict__ acol, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  TileSlot* slots = reinterpret_cast<TileSlot*>(smem + SLOT_OFF);
+  StageInfo* info = reinterpret_cast<StageInfo*>(smem + INFO_OFF);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BAR_OFF);
+  // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], mma_fin, slot_full[2], slot_empty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 9);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
@@ -236,16 +247,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   auto empty = [&](int s) { return saddr(&bars[STAGES + s]); };
   auto acc_full = [&](int b) { return saddr(&bars[2 * STAGES + b]); };
   auto acc_empty = [&](int b) { return saddr(&bars[2 * STAGES + 2 + b]); };
+  const uint32_t mma_fin = saddr(&bars[2 * STAGES + 4]);
+  auto slot_full = [&](int b) { return saddr(&bars[2 * STAGES + 5 + b]); };
+  auto slot_empty = [&](int b) { return saddr(&bars[2 * STAGES + 7 + b]); };
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full(s), PRODUCER_WARPS);
+      mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full(b), 1);
       mbar_init(acc_empty(b), DRAIN_THREADS / 32);
+      mbar_init(slot_full(b), 1);
+      mbar_init(slot_empty(b), DRAIN_THREADS / 32);
     }
+    mbar_init(mma_fin, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -261,57 +278,43 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ---- MMA issuer
+    // ---- MMA issuer: consumes the ring in order, driven by the stage control
+    // words alone (no global loads on the tensor core's critical path)
     if (lane == 0) {
-      int step = 0;     // global stage counter (ring position)
-      int chunk = 0;    // global chunk counter (accumulator buffer rotation)
-      for (int ti = blockIdx.x; ti < ntiles; ti += G) {
-        const MixTile tl = tiles[ti];
-        const MixProb p = probs[tl.prob];
-        const int Nt = min(MIX_TN, p.N - tl.n0);
-        const uint32_t id = idesc((Nt + 15) & ~15);
-        int in_chunk = 0;
-        uint32_t dbase = 0;
-        for (int s = p.s0; s < p.s1; ++s) {
-          const int K = segs[s].K;
-          for (int k0 = 0; k0 < K; k0 += BK, ++step) {
-            if (in_chunk == 0) {
-              const int b = chunk & 1, use = chunk >> 1;
-              if (use > 0 && !mbar_wait(acc_empty(b), (use - 1) & 1, abort_flag, err, 4)) goto mma_done;
-              dbase = tmem + 256u * b;
-            }
-            const int st = step % STAGES;
-            if (!mbar_wait(full(st), (step / STAGES) & 1, abort_flag, err, 1)) goto mma_done;
-            // the stage was written by cp.async (generic proxy); order it before the
-            // tensor core's async-proxy reads
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            fence_after();
-            const uint32_t base = saddr(smem + st * STAGE_BYTES);
-            const int ksub = (K - k0 > 16) ? 2 : 1;
-            for (int kk = 0; kk < ksub; ++kk) {
-              const uint32_t o = kk * 256;
-              const uint64_t a0 = sdesc(base + o), a1 = sdesc(base + PLANE_BYTES + o),
-                             a2 = sdesc(base + 2 * PLANE_BYTES + o);
-              const uint64_t b0 = sdesc(base + 3 * PLANE_BYTES + o), b1 = sdesc(base + 4 * PLANE_BYTES + o),
-                             b2 = sdesc(base + 5 * PLANE_BYTES + o);
-              const uint32_t acc = (in_chunk == 0 && kk == 0) ? 0u : 1u;
-              mma(dbase, a0, b0, id, acc);
-              mma(dbase + 128, a0, b1, id, acc);
-              mma(dbase + 128, a1, b0, id, 1u);
-              mma(dbase + 128, a0, b2, id, 1u);
-              mma(dbase + 128, a1, b1, id, 1u);
-              mma(dbase + 128, a2, b0, id, 1u);
-            }
-            mma_commit(empty(st));
-            if (++in_chunk == CHUNK) {
-              mma_commit(acc_full(chunk & 1));
-              in_chunk = 0;
-              ++chunk;
-            }
-          }
+      int step = 0;      // global stage counter (ring position)
+      int chunk = 0;     // global chunk counter (accumulator buffer rotation)
+      int in_chunk = 0;
+      uint32_t dbase = 0;
+      for (;; ++step) {
+        const int st = step % STAGES;
+        if (!mbar_wait(full(st), (step / STAGES) & 1, abort_flag, err, 1)) goto mma_done;
+        const StageInfo si = info[st];
+        if (si.ksub == 0) break;
+        if (in_chunk == 0) {
+          const int b = chunk & 1, use = chunk >> 1;
+          if (use > 0 && !mbar_wait(acc_empty(b), (use - 1) & 1, abort_flag, err, 4)) goto mma_done;
+          dbase = tmem + 256u * b;
         }
-        if (in_chunk > 0) {
+        fence_after();
+        const uint32_t id = idesc(si.nmma);
+        const uint32_t base = saddr(smem + st * STAGE_BYTES);
+        for (int kk = 0; kk < si.ksub; ++kk) {
+          const uint32_t o = kk * 256;
+          const uint64_t a0 = sdesc(base + o), a1 = sdesc(base + 512 + o), a2 = sdesc(base + 1024 + o);
+          const uint64_t b0 = sdesc(base + OPER_BYTES + o), b1 = sdesc(base + OPER_BYTES + 512 + o),
+                         b2 = sdesc(base + OPER_BYTES + 1024 + o);
+          const uint32_t acc = (in_chunk == 0 && kk == 0) ? 0u : 1u;
+          mma(dbase, a0, b0, id, acc);
+          mma(dbase + 128, a0, b1, id, acc);
+          mma(dbase + 128, a1, b0, id, 1u);
+          mma(dbase + 128, a0, b2, id, 1u);
+          mma(dbase + 128, a1, b1, id, 1u);
+          mma(dbase + 128, a2, b0, id, 1u);
+        }
+        mma_commit(empty(st));
+        if (++in_chunk == CHUNK || si.last) {
           mma_commit(acc_full(chunk & 1));
+          in_chunk = 0;
           ++chunk;
         }
       }
@@ -319,102 +322,163 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     mma_done:
       *abort_flag = 1;
       mma_commit(acc_full(chunk & 1));
-    mma_end:;
+    mma_end:
+      // every MMA this thread issued has finished before TMEM is released
+      mma_commit(mma_fin);
+      mbar_wait_exit(mma_fin, 0, err);
     }
     __syncwarp();
-  } else if (warp < 1 + PRODUCER_WARPS) {
-    // ---- producers
-    const int pt = tid - 32;
-    int step = 0;
+  } else if (warp == 1) {
+    // ---- producer warp: the only role that reads the plan from global memory.
+    // Per tile it fills a tile slot for the drain warps (problem fields, and for
+    // gathered problems the column tables by bulk copy); per stage it writes the
+    // control word and copies the operand slabs: the slab of a 128-row operand
+    // tile is contiguous in HBM (blocked split layout), so a stage is one bulk copy
+    // for A and one for B (one per 8-row group for gathered A rows), completing on
+    // the stage's transaction count.  The next tiles' records are prefetched one
+    // and two tiles ahead.
+    int step = 0, tcount = 0;
     bool stop = false;
-    for (int ti = blockIdx.x; ti < ntiles && !stop; ti += G) {
-      const MixTile tl = tiles[ti];
-      const MixProb p = probs[tl.prob];
+    const int t0 = blockIdx.x;
+    MixTile t1{}, t2{};
+    MixProb p1{};
+    MixSeg g1{};
+    if (t0 < ntiles) {
+      t1 = tiles[t0];
+      p1 = probs[t1.prob];
+      if (p1.s1 > p1.s0) g1 = segs[p1.s0];
+    }
+    if (t0 + G < ntiles) t2 = tiles[t0 + G];
+    for (int ti = t0; ti < ntiles && !stop; ti += G, ++tcount) {
+      const MixTile tl = t1;
+      const MixProb p = p1;
+      const MixSeg gf = g1;
+      if (ti + G < ntiles) {
+        t1 = t2;
+        p1 = probs[t1.prob];
+        if (p1.s1 > p1.s0) g1 = segs[p1.s0];
+        if (ti + 2 * G < ntiles) t2 = tiles[ti + 2 * G];
+      }
+      const int slot = tcount & 1;
+      if (tcount >= 2 && !mbar_wait_warp(slot_empty(slot), ((tcount >> 1) - 1) & 1, abort_flag, err, 6)) {
+        stop = true;
+        break;
+      }
       const int Nt = min(MIX_TN, p.N - tl.n0);
-      const int Nmma = (Nt + 15) & ~15;
+      if (lane == 0) {
+        TileSlot& sl = slots[slot];
+        sl.Chi = p.Chi;
+        sl.Clo = p.Clo;
+        sl.Cp = p.Cp;
+        sl.m0 = tl.m0;
+        sl.n0 = tl.n0;
+        sl.Nt = Nt;
+        sl.nch = (tl.nsteps + CHUNK - 1) / CHUNK;
+        sl.M = p.M;
+        sl.ldc = p.ldc;
+        sl.mode = p.mode;
+        sl.row0 = p.row0;
+        sl.crows = p.crows;
+        sl.alpha = p.alpha;
+        if (p.mode == 3) {
+          const int Mt = min(MIX_TM, p.M - tl.m0);
+          mbar_expect_tx(slot_full(slot), uint32_t(Mt) * 12u);
+          bulk_copy(saddr(sl.c), ccol + p.cm0 + tl.m0, uint32_t(Mt) * 8u, slot_full(slot));
+          bulk_copy(saddr(sl.a), acol + p.cm0 + tl.m0, uint32_t(Mt) * 4u, slot_full(slot));
+        } else {
+          mbar_arrive(slot_full(slot));
+        }
+      }
+      const int hA = min(MIX_TM, ((p.M + 7) & ~7) - tl.m0);   // rows of A in the tile (multiple of 8)
+      const int hB = min(MIX_TN, ((p.N + 7) & ~7) - tl.n0);
+      const int64_t u0 = p.cm0 / 8 + (tl.m0 >> 3);            // first gathered unit of the tile
+      const int nmma = (Nt + 15) & ~15;
+      int left = tl.nsteps;
       for (int s = p.s0; s < p.s1 && !stop; ++s) {
-        const MixSeg g = segs[s];
-        const int Kp = (g.K + 7) & ~7;
+        const MixSeg g = (s == p.s0) ? gf : segs[s];
+        const int64_t Kt = (g.K + 31) & ~31;
+        const uint16_t* Ab = g.A + int64_t(tl.m0 >> 7) * 384 * Kt;
+        const uint16_t* Bb = g.B + int64_t(tl.n0 >> 7) * 384 * Kt;
         for (int k0 = 0; k0 < g.K; k0 += BK, ++step) {
           const int st = step % STAGES;
           if (step >= STAGES && !mbar_wait_warp(empty(st), ((step / STAGES) - 1) & 1, abort_flag, err, 2)) {
             stop = true;
             break;
           }
+          const bool last = (--left == 0);
           const uint32_t base = saddr(smem + st * STAGE_BYTES);
-          for (int idx = pt; idx < 512; idx += PRODUCER_THREADS) {
-            const int r = idx >> 2, j = idx & 3;
-            const int k = k0 + 8 * j;
-            const uint32_t so = (((r >> 3) * (BK / 8) + j) << 7) + ((r & 7) << 4);
-            const int gm = tl.m0 + r, gn = tl.n0 + r;
-            const bool va = gm < p.M && k < Kp;
-            const bool vb = r < Nmma && gn < p.N && k < Kp;
-            // out-of-range chunks are zero-filled (source size 0, base pointer as a valid address)
-            const uint16_t* a = va ? g.A + int64_t(gm) * g.lda + k : g.A;
-            const uint16_t* bb =
-                vb ? g.B + (p.mode == 3 ? bcol[p.cm0 + gn] : int64_t(gn) * g.ldb) + k : g.B;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              cp_async16(base + q * PLANE_BYTES + so, a + q * g.psA, va ? 16u : 0u);
-              cp_async16(base + (3 + q) * PLANE_BYTES + so, bb + q * g.psB, vb ? 16u : 0u);
-            }
+          const int64_t sl = k0 >> 5;
+          if (lane == 0) {
+            info[st] = StageInfo{(g.K - k0 > 16) ? 2 : 1, last ? 1 : 0, nmma, 0};
+            mbar_expect_tx(full(st), uint32_t(hA + hB) * 192u);
+            if (p.mode != 3) bulk_copy(base, Ab + sl * 96 * hA, uint32_t(hA) * 192u, full(st));
+            bulk_copy(base + OPER_BYTES, Bb + sl * 96 * hB, uint32_t(hB) * 192u, full(st));
           }
-          // one commit group per stage; the stage issued LAG steps ago is retired when
-          // its group has landed: the warp syncs and one lane arrives on its full barrier
-          asm volatile("cp.async.commit_group;" ::: "memory");
-          if (step >= LAG) {
-            asm volatile("cp.async.wait_group %0;" ::"n"(LAG) : "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(full((step - LAG) % STAGES));
+          __syncwarp();   // the transaction count is raised before the gathered copies
+          if (p.mode == 3 && lane < (hA >> 3)) {
+            const int64_t b0 = bcol[2 * (u0 + lane)], bs = bcol[2 * (u0 + lane) + 1];
+            bulk_copy(base + lane * RG_BYTES, g.A + b0 + sl * bs, RG_BYTES, full(st));
           }
         }
       }
     }
-    // retire the last stages in order
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!stop) {
+      // end marker for the MMA issuer
+      const int st = step % STAGES;
+      if (step < STAGES || mbar_wait_warp(empty(st), ((step / STAGES) - 1) & 1, abort_flag, err, 2)) {
+        if (lane == 0) {
+          info[st] = StageInfo{0, 0, 0, 0};
+          mbar_arrive(full(st));
+        }
+        ++step;
+      }
+    }
+    // no copy into this CTA's shared memory may still be in flight at exit: wait for
+    // the last issued stages and tile slots (already complete unless a role aborted)
+    if (lane == 0) {
+      for (int s = max(0, step - STAGES); s < step; ++s) mbar_wait_exit(full(s % STAGES), (s / STAGES) & 1, err);
+      for (int t = max(0, tcount - 2); t < tcount; ++t) mbar_wait_exit(slot_full(t & 1), (t >> 1) & 1, err);
+    }
     __syncwarp();
-    if (lane == 0)
-      for (int r = (step > LAG ? step - LAG : 0); r < step; ++r) mbar_arrive(full(r % STAGES));
   } else {
     // ---- drain + epilogue
-    const int dw = warp - 1 - PRODUCER_WARPS;   // 0..7
+    const int dw = warp - 2;                     // 0..15
     const int q4 = warp & 3;                     // TMEM lane quarter of this warp
-    const int ch = dw >> 2;                      // column half: columns [64 ch, 64 ch + 64)
+    const int ch = dw >> 2;                      // column quarter: [32 ch, 32 ch + 32)
     const int row = q4 * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
-    int chunk = 0;
+    int chunk = 0, tcount = 0;
     bool ok = true;
-    for (int ti = blockIdx.x; ti < ntiles; ti += G) {
-      const MixTile tl = tiles[ti];
-      const MixProb p = probs[tl.prob];
-      const int Nt = min(MIX_TN, p.N - tl.n0);
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += G, ++tcount) {
+      const int slot = tcount & 1;
+      ok = mbar_wait_warp(slot_full(slot), (tcount >> 1) & 1, abort_flag, err, 7);
+      if (!ok) break;
+      const TileSlot& S = slots[slot];
+      const int Nt = S.Nt, nch = S.nch;
       const int Nmma = (Nt + 15) & ~15;
-      int nsteps = 0;
-      for (int s = p.s0; s < p.s1; ++s) nsteps += (segs[s].K + BK - 1) / BK;
-      const int nch = (nsteps + CHUNK - 1) / CHUNK;
-      float sh[64], sl[64];
+      // running sum per element: sh + sl, where sh collects the hi x hi chunks
+      // exactly (TwoSum) and sl their rounding errors plus the small products,
+      // which are 2^-8 of the result and need no more than FP32
+      float sh[DRAIN_COLS], sl[DRAIN_COLS];
 #pragma unroll
-      for (int i = 0; i < 64; ++i) sh[i] = sl[i] = 0.f;
-      const bool mine = 64 * ch < Nmma;          // this warp's columns exist in the tile
+      for (int i = 0; i < DRAIN_COLS; ++i) sh[i] = sl[i] = 0.f;
+      const bool mine = DRAIN_COLS * ch < Nmma;  // this warp's columns exist in the tile
       for (int c = 0; c < nch; ++c, ++chunk) {
         const int b = chunk & 1, use = chunk >> 1;
         if (ok) ok = mbar_wait_warp(acc_full(b), use & 1, abort_flag, err, 3);
         fence_after();
         if (ok && mine) {
-          const uint32_t t0 = tmem + lane_off + 256u * b + 64u * ch;
+          const uint32_t t0 = tmem + lane_off + 256u * b + uint32_t(DRAIN_COLS) * ch;
 #pragma unroll
-          for (int h = 0; h < 8; ++h) {
+          for (int h = 0; h < DRAIN_COLS / 8; ++h) {
             float v0[8], v1[8];
             tmem_ld2x8(t0 + 8 * h, t0 + 128 + 8 * h, v0, v1);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              float hi, lo;
-              two_sum(v0[i], v1[i], hi, lo);
               float s, e;
-              two_sum(sh[8 * h + i], hi, s, e);
-              e += sl[8 * h + i] + lo;
-              sh[8 * h + i] = s + e;
-              sl[8 * h + i] = e - (sh[8 * h + i] - s);
+              two_sum(sh[8 * h + i], v0[i], s, e);
+              sh[8 * h + i] = s;
+              sl[8 * h + i] += e + v1[i];
             }
           }
         }
@@ -423,70 +487,70 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) mbar_arrive(acc_empty(b));
       }
       // epilogue: this thread owns row `row`, columns n0 + 32 ch + i
-      const int gm = tl.m0 + row;
-      if (!mine || gm >= p.M) continue;
-      const int cbase = 64 * ch;
-      if (p.mode == 0) {
+      const int gm = S.m0 + row;
+      const int cbase = DRAIN_COLS * ch;
+      if (ok && mine && gm < S.M) {
+        const float alpha = S.alpha;
+        if (S.mode == 0) {
+          float* Chi = S.Chi;
+          float* Clo = S.Clo;
+          const int64_t o0 = int64_t(gm) * S.ldc + S.n0 + cbase;
 #pragma unroll
-        for (int i = 0; i < 64; ++i) {
-          if (cbase + i >= Nt) break;
-          const int64_t o = int64_t(gm) * p.ldc + tl.n0 + cbase + i;
-          float hi = p.alpha * sh[i], lo = p.alpha * sl[i];
-          if (p.accumulate) {
-            float s, e;
-            two_sum(p.Chi[o], hi, s, e);
-            e += p.Clo[o] + lo;
-            hi = s + e;
-            lo = e - (hi - s);
+          for (int i = 0; i < DRAIN_COLS; ++i) {
+            if (cbase + i >= Nt) break;
+            float hi, lo;
+            two_sum(alpha * sh[i], alpha * sl[i], hi, lo);
+            Chi[o0 + i] = hi;
+            Clo[o0 + i] = lo;
           }
-          p.Chi[o] = hi;
-          p.Clo[o] = lo;
-        }
-      } else if (p.mode == 1 && cbase + 64 <= Nt) {
-        // 64 consecutive BF16 per plane as eight 16-byte stores (row starts and
-        // column offsets are multiples of 8 elements in every plane layout)
-        uint16_t* dst = p.Cp + int64_t(gm) * p.ldc + tl.n0 + cbase;
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          uint32_t hw[4], mw[4], lw[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            uint16_t hh[2], mm[2], ll[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int c = 8 * v + 2 * i + u;
-              split3(p.alpha * sh[c], p.alpha * sl[c], hh[u], mm[u], ll[u]);
-            }
-            hw[i] = hh[0] | (uint32_t(hh[1]) << 16);
-            mw[i] = mm[0] | (uint32_t(mm[1]) << 16);
-            lw[i] = ll[0] | (uint32_t(ll[1]) << 16);
-          }
-          reinterpret_cast<uint4*>(dst)[v] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          reinterpret_cast<uint4*>(dst + p.psC)[v] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
-          reinterpret_cast<uint4*>(dst + 2 * p.psC)[v] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        }
-      } else {
-        // mode 1 tail, mode 2 (transposed store: tile column n goes to row n of C) or
-        // mode 3 (column n goes to the row of C given by its table entry)
-#pragma unroll
-        for (int i = 0; i < 64; ++i) {
-          if (cbase + i >= Nt) break;
-          const int n = tl.n0 + cbase + i;
-          int64_t o;
-          float al = p.alpha;
-          if (p.mode == 3) {
-            o = ccol[p.cm0 + n] + gm;
-            al = acol[p.cm0 + n];
+        } else if (cbase < Nt) {
+          // modes 2 and 3: tile row gm is row r of the blocked split matrix C (mode
+          // 2: r = row0 + gm; mode 3: row part and row-block height from the
+          // table) and this thread's 32 columns are one K slab of it, so each of
+          // the three planes is four aligned 16-byte runs
+          int64_t rowpart = 0;
+          int h = 0;
+          float al = alpha;
+          bool store = true;
+          if (S.mode == 3) {
+            const int64_t e = S.c[gm - S.m0];
+            store = e >= 0;
+            rowpart = e & ((int64_t(1) << 48) - 1);
+            h = 8 * int(e >> 48);
+            al = S.a[gm - S.m0];
           } else {
-            o = (p.mode == 2) ? int64_t(n) * p.ldc + gm : int64_t(gm) * p.ldc + n;
+            const int r = S.row0 + gm, rb = r >> 7, rr = r & 127;
+            h = min(128, S.crows - (rb << 7));
+            rowpart = int64_t(rb) * 384 * S.ldc + (rr >> 3) * 768 + (rr & 7) * 8;
           }
-          uint16_t h, m, l;
-          split3(al * sh[i], al * sl[i], h, m, l);
-          p.Cp[o] = h;
-          p.Cp[o + p.psC] = m;
-          p.Cp[o + 2 * p.psC] = l;
+          if (store) {
+            uint16_t* dst = S.Cp + rowpart + int64_t((S.n0 + cbase) >> 5) * 96 * h;
+#pragma unroll
+            for (int j = 0; j < DRAIN_COLS / 8; ++j) {
+              uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                uint16_t hh[2], mm[2], ll[2];
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                  const int i = 8 * j + 2 * u + v;
+                  float hi, lo;
+                  two_sum(al * sh[i], al * sl[i], hi, lo);
+                  split3(hi, lo, hh[v], mm[v], ll[v]);
+                }
+                hw[u] = hh[0] | (uint32_t(hh[1]) << 16);
+                mw[u] = mm[0] | (uint32_t(mm[1]) << 16);
+                lw[u] = ll[0] | (uint32_t(ll[1]) << 16);
+              }
+              *reinterpret_cast<uint4*>(dst + 64 * j) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(dst + 256 + 64 * j) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+              *reinterpret_cast<uint4*>(dst + 512 + 64 * j) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+          }
         }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(slot_empty(slot));
     }
   }
   fence_before();
@@ -510,16 +574,16 @@ __global__ void split_kernel(const SplitTask* __restrict__ t, int nt) {
       const double r2 = r1 - static_cast<double>(__bfloat162float(m));
       const __nv_bfloat16 l = __double2bfloat16(r2);
       if (s.dn) {
-        uint16_t* d = s.dn + int64_t(r) * s.ldn + c;
+        uint16_t* d = s.dn + blk_off(0, s.rn0 + r, s.cn0 + c, s.rn8, s.ktn);
         d[0] = bf_bits(h);
-        d[s.ps] = bf_bits(m);
-        d[2 * s.ps] = bf_bits(l);
+        d[256] = bf_bits(m);
+        d[512] = bf_bits(l);
       }
       if (s.dt) {
-        uint16_t* d = s.dt + int64_t(c) * s.ldt + r;
+        uint16_t* d = s.dt + blk_off(0, s.rt0 + c, s.ct0 + r, s.rt8, s.ktt);
         d[0] = bf_bits(h);
-        d[s.ps] = bf_bits(m);
-        d[2 * s.ps] = bf_bits(l);
+        d[256] = bf_bits(m);
+        d[512] = bf_bits(l);
       }
     }
   }

@@ -9,7 +9,8 @@
 namespace dmrg {
 
 struct MixTile {
-  int prob, m0, n0, pad;
+  int prob, m0, n0;
+  int nsteps;   // K stages of the tile (sum over its segments of ceil(K / 32))
 };
 
 // launch the grouped split-BF16 GEMM over `ntiles` tiles; err is a device int
