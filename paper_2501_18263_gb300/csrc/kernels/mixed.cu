@@ -29,7 +29,7 @@ namespace dmrg {
 namespace {
 
 constexpr int BK = 32;                          // K elements per stage (one K slab)
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int RG_BYTES = 3 * 8 * BK * 2;        // one 8-row group of a slab, three planes: 1536 B
 constexpr int OPER_BYTES = 16 * RG_BYTES;       // a 128-row operand slab: 24 KiB
 constexpr int STAGE_BYTES = 2 * OPER_BYTES;     // A and B
@@ -38,7 +38,7 @@ constexpr int DRAIN_THREADS = 512;              // 16 warps: 4 lane quarters x 4
 constexpr int DRAIN_COLS = 32;                  // accumulator columns per drain thread
 constexpr int NTHREADS = 32 + 32 + DRAIN_THREADS;
 constexpr int CHUNK = 4;                        // K stages per accumulator chunk (128 K)
-constexpr long long WAIT_CYCLES = 4000000000LL; // about 2 s at 2 GHz
+constexpr long long WAIT_CYCLES = 3000000000LL; // about 1.5 s at 2 GHz (fits the 32-bit clock)
 constexpr uint32_t TMEM_COLS = 512;
 
 static_assert(MIX_TN == MIX_TM && MIX_TM == 128, "tiles are 128 x 128");
@@ -93,19 +93,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait: gives up after WAIT_CYCLES or when another role aborted
-__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* err, int code) {
+// bounded wait: gives up after about WAIT_CYCLES SM cycles (32-bit clock, one
+// wrap allowed) or when another role aborted, then raises the abort flag and
+// records `code`.  Kept small in registers: the drain warps wait while holding
+// their accumulator sums.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code) {
   if (mbar_try(a, parity)) return true;
-  const long long t0 = clock64();
-  for (unsigned spin = 1;; ++spin) {
+  const uint32_t t0 = static_cast<uint32_t>(clock());
+  for (uint32_t spin = 1;; ++spin) {
     if (mbar_try(a, parity)) return true;
-    if ((spin & 255u) == 0) {
-      if (*abort_flag) return false;
-      if (clock64() - t0 > WAIT_CYCLES) {
+    if ((spin & 255u) == 0 &&
+        (*abort_flag || static_cast<uint32_t>(clock()) - t0 > static_cast<uint32_t>(WAIT_CYCLES))) {
+      if (!*abort_flag) {
         *abort_flag = 1;
         atomicExch(err, code);
-        return false;
       }
+      return false;
     }
   }
 }
@@ -216,6 +220,20 @@ __device__ __forceinline__ void tmem_ld2x8(uint32_t t0, uint32_t t1, float* v0, 
     v0[i] = __uint_as_float(a[i]);
     v1[i] = __uint_as_float(b[i]);
   }
+}
+
+// two 32-lane x 8-column stores and the wait, in one statement
+__device__ __forceinline__ void tmem_st2x8(uint32_t t0, uint32_t t1, const float* v0, const float* v1) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%16], {%0,%1,%2,%3,%4,%5,%6,%7};\n\t"
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%17], {%8,%9,%10,%11,%12,%13,%14,%15};\n\t"
+      "tcgen05.wait::st.sync.aligned;\n" ::"r"(__float_as_uint(v0[0])),
+      "r"(__float_as_uint(v0[1])), "r"(__float_as_uint(v0[2])), "r"(__float_as_uint(v0[3])),
+      "r"(__float_as_uint(v0[4])), "r"(__float_as_uint(v0[5])), "r"(__float_as_uint(v0[6])),
+      "r"(__float_as_uint(v0[7])), "r"(__float_as_uint(v1[0])), "r"(__float_as_uint(v1[1])),
+      "r"(__float_as_uint(v1[2])), "r"(__float_as_uint(v1[3])), "r"(__float_as_uint(v1[4])),
+      "r"(__float_as_uint(v1[5])), "r"(__float_as_uint(v1[6])), "r"(__float_as_uint(v1[7])), "r"(t0), "r"(t1)
+      : "memory");
 }
 
 // Persistent split-BF16 grouped GEMM.  Grid = min(#tiles, #SMs); CTA c takes the
@@ -441,107 +459,135 @@ __global__ void __maxnreg__(96)
     }
     __syncwarp();
   } else {
-    // ---- drain + epilogue
+    // ---- drain + epilogue.  After an abort every wait returns at once; TMEM
+    // contents are then meaningless but every store still goes to the addresses of
+    // a tile slot that did arrive, and the tile loop ends at the next check.
     const int dw = warp - 2;                     // 0..15
-    const int q4 = warp & 3;                     // TMEM lane quarter of this warp
     const int ch = dw >> 2;                      // column quarter: [32 ch, 32 ch + 32)
-    const int row = q4 * 32 + lane;
-    const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
+    const int row = (warp & 3) * 32 + lane;      // TMEM lane quarter = warp % 4
+    const uint32_t tq = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + uint32_t(DRAIN_COLS * ch);
     int chunk = 0, tcount = 0;
-    bool ok = true;
-    for (int ti = blockIdx.x; ti < ntiles && ok; ti += G, ++tcount) {
+    for (int ti = blockIdx.x; ti < ntiles; ti += G, ++tcount) {
       const int slot = tcount & 1;
-      ok = mbar_wait_warp(slot_full(slot), (tcount >> 1) & 1, abort_flag, err, 7);
-      if (!ok) break;
+      if (!mbar_wait_warp(slot_full(slot), (tcount >> 1) & 1, abort_flag, err, 7)) break;
       const TileSlot& S = slots[slot];
-      const int Nt = S.Nt, nch = S.nch;
-      const int Nmma = (Nt + 15) & ~15;
+      const int nch = S.nch;
+      const bool mine = DRAIN_COLS * ch < S.Nt;  // this warp's columns exist in the tile
       // running sum per element: sh + sl, where sh collects the hi x hi chunks
       // exactly (TwoSum) and sl their rounding errors plus the small products,
-      // which are 2^-8 of the result and need no more than FP32
-      float sh[DRAIN_COLS], sl[DRAIN_COLS];
+      // which are 2^-8 of the result and need no more than FP32.  After the last
+      // chunk the sums are parked in that chunk's accumulator columns (sh over
+      // acc0, sl over acc1) and the epilogue streams them out of TMEM, so that no
+      // more than eight columns are live in registers while it stores.
+      {
+        float sh[DRAIN_COLS], sl[DRAIN_COLS];
 #pragma unroll
-      for (int i = 0; i < DRAIN_COLS; ++i) sh[i] = sl[i] = 0.f;
-      const bool mine = DRAIN_COLS * ch < Nmma;  // this warp's columns exist in the tile
-      for (int c = 0; c < nch; ++c, ++chunk) {
-        const int b = chunk & 1, use = chunk >> 1;
-        if (ok) ok = mbar_wait_warp(acc_full(b), use & 1, abort_flag, err, 3);
-        fence_after();
-        if (ok && mine) {
-          const uint32_t t0 = tmem + lane_off + 256u * b + uint32_t(DRAIN_COLS) * ch;
+        for (int i = 0; i < DRAIN_COLS; ++i) sh[i] = sl[i] = 0.f;
+        for (int c = 0; c < nch; ++c, ++chunk) {
+          const int b = chunk & 1;
+          mbar_wait_warp(acc_full(b), (chunk >> 1) & 1, abort_flag, err, 3);
+          fence_after();
+          const uint32_t t0 = tq + 256u * b;
+          if (mine) {
 #pragma unroll
-          for (int h = 0; h < DRAIN_COLS / 8; ++h) {
-            float v0[8], v1[8];
-            tmem_ld2x8(t0 + 8 * h, t0 + 128 + 8 * h, v0, v1);
+            for (int h = 0; h < DRAIN_COLS / 8; ++h) {
+              float v0[8], v1[8];
+              tmem_ld2x8(t0 + 8 * h, t0 + 128 + 8 * h, v0, v1);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              float s, e;
-              two_sum(sh[8 * h + i], v0[i], s, e);
-              sh[8 * h + i] = s;
-              sl[8 * h + i] += e + v1[i];
+              for (int i = 0; i < 8; ++i) {
+                float s, e;
+                two_sum(sh[8 * h + i], v0[i], s, e);
+                sh[8 * h + i] = s;
+                sl[8 * h + i] += e + v1[i];
+              }
+              if (c == nch - 1) tmem_st2x8(t0 + 8 * h, t0 + 128 + 8 * h, sh + 8 * h, sl + 8 * h);
             }
           }
+          if (c < nch - 1) {
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty(b));
+          }
         }
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(acc_empty(b));
       }
-      // epilogue: this thread owns row `row`, columns n0 + 32 ch + i
+      // epilogue: this thread owns row `row`, columns n0 + 32 ch + i.  The TMEM
+      // loads are warp-collective (.sync.aligned), so they run under the
+      // warp-uniform `mine` alone and rows past M only skip their stores.
       const int gm = S.m0 + row;
+      const bool live = gm < S.M;
       const int cbase = DRAIN_COLS * ch;
-      if (ok && mine && gm < S.M) {
+      const uint32_t tl = tq + 256u * uint32_t((chunk - 1) & 1);   // parked sums (nch > 0)
+      if (mine) {
         const float alpha = S.alpha;
         if (S.mode == 0) {
           float* Chi = S.Chi;
           float* Clo = S.Clo;
           const int64_t o0 = int64_t(gm) * S.ldc + S.n0 + cbase;
+          const int nloc = min(DRAIN_COLS, S.Nt - cbase);
 #pragma unroll
-          for (int i = 0; i < DRAIN_COLS; ++i) {
-            if (cbase + i >= Nt) break;
-            float hi, lo;
-            two_sum(alpha * sh[i], alpha * sl[i], hi, lo);
-            Chi[o0 + i] = hi;
-            Clo[o0 + i] = lo;
+          for (int h = 0; h < DRAIN_COLS / 8; ++h) {
+            float v0[8], v1[8];
+            if (nch > 0) {
+              tmem_ld2x8(tl + 8 * h, tl + 128 + 8 * h, v0, v1);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) v0[i] = v1[i] = 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              if (live && 8 * h + i < nloc) {
+                float hi, lo;
+                two_sum(alpha * v0[i], alpha * v1[i], hi, lo);
+                Chi[o0 + 8 * h + i] = hi;
+                Clo[o0 + 8 * h + i] = lo;
+              }
+            }
           }
-        } else if (cbase < Nt) {
+        } else {
           // modes 2 and 3: tile row gm is row r of the blocked split matrix C (mode
           // 2: r = row0 + gm; mode 3: row part and row-block height from the
           // table) and this thread's 32 columns are one K slab of it, so each of
           // the three planes is four aligned 16-byte runs
           int64_t rowpart = 0;
-          int h = 0;
+          int h8 = 0;
           float al = alpha;
-          bool store = true;
+          bool store = live;
           if (S.mode == 3) {
-            const int64_t e = S.c[gm - S.m0];
+            const int64_t e = live ? S.c[gm - S.m0] : -1;
             store = e >= 0;
             rowpart = e & ((int64_t(1) << 48) - 1);
-            h = 8 * int(e >> 48);
-            al = S.a[gm - S.m0];
-          } else {
+            h8 = 8 * int(e >> 48);
+            al = live ? S.a[gm - S.m0] : 0.f;
+          } else if (live) {
             const int r = S.row0 + gm, rb = r >> 7, rr = r & 127;
-            h = min(128, S.crows - (rb << 7));
+            h8 = min(128, S.crows - (rb << 7));
             rowpart = int64_t(rb) * 384 * S.ldc + (rr >> 3) * 768 + (rr & 7) * 8;
           }
-          if (store) {
-            uint16_t* dst = S.Cp + rowpart + int64_t((S.n0 + cbase) >> 5) * 96 * h;
+          uint16_t* dst = S.Cp + rowpart + int64_t((S.n0 + cbase) >> 5) * 96 * h8;
 #pragma unroll
-            for (int j = 0; j < DRAIN_COLS / 8; ++j) {
-              uint32_t hw[4], mw[4], lw[4];
+          for (int j = 0; j < DRAIN_COLS / 8; ++j) {
+            float v0[8], v1[8];
+            if (nch > 0) {
+              tmem_ld2x8(tl + 8 * j, tl + 128 + 8 * j, v0, v1);
+            } else {
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                uint16_t hh[2], mm[2], ll[2];
+              for (int i = 0; i < 8; ++i) v0[i] = v1[i] = 0.f;
+            }
+            uint32_t hw[4], mw[4], lw[4];
 #pragma unroll
-                for (int v = 0; v < 2; ++v) {
-                  const int i = 8 * j + 2 * u + v;
-                  float hi, lo;
-                  two_sum(al * sh[i], al * sl[i], hi, lo);
-                  split3(hi, lo, hh[v], mm[v], ll[v]);
-                }
-                hw[u] = hh[0] | (uint32_t(hh[1]) << 16);
-                mw[u] = mm[0] | (uint32_t(mm[1]) << 16);
-                lw[u] = ll[0] | (uint32_t(ll[1]) << 16);
+            for (int u = 0; u < 4; ++u) {
+              uint16_t hh[2], mm[2], ll[2];
+#pragma unroll
+              for (int v = 0; v < 2; ++v) {
+                float hi, lo;
+                two_sum(al * v0[2 * u + v], al * v1[2 * u + v], hi, lo);
+                split3(hi, lo, hh[v], mm[v], ll[v]);
               }
+              hw[u] = hh[0] | (uint32_t(hh[1]) << 16);
+              mw[u] = mm[0] | (uint32_t(mm[1]) << 16);
+              lw[u] = ll[0] | (uint32_t(ll[1]) << 16);
+            }
+            if (store) {
               *reinterpret_cast<uint4*>(dst + 64 * j) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
               *reinterpret_cast<uint4*>(dst + 256 + 64 * j) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
               *reinterpret_cast<uint4*>(dst + 512 + 64 * j) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -549,8 +595,13 @@ __global__ void __maxnreg__(96)
           }
         }
       }
+      fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(slot_empty(slot));
+      if (lane == 0) {
+        if (nch > 0) mbar_arrive(acc_empty((chunk - 1) & 1));
+        mbar_arrive(slot_empty(slot));
+      }
+      if (*abort_flag) break;
     }
   }
   fence_before();
