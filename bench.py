@@ -17,6 +17,7 @@ path); timing is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -48,6 +49,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 sigma steps timed beside the mixed ones")
     ap.add_argument("--cpu-sample", default="12,6,6,256", help="L,na,nb,D of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweeps", type=int, default=0,
+                    help="also time this many full two-site sweeps at bond dimension D (fresh seeded basis)")
+    ap.add_argument("--sweep-tol", type=float, default=1e-6, help="Davidson residual tolerance of the timed sweeps")
     a = ap.parse_args()
     a.na = a.L // 2 if a.na is None else a.na
     a.nb = a.L // 2 if a.nb is None else a.nb
@@ -113,6 +117,23 @@ class Clocks:
                     reasons.add(n)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_traffic(args, mixed):
+    """DRAM bytes per sigma of the tensor-core kernel from the committed ncu capture of
+    this workload, or None when the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "mixed_gemm_kernel_L32_D2048.json")
+    try:
+        rec = json.load(open(path))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        w = rec["workload"]
+        if (not mixed or hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"] or
+                (w["L"], w["n_alpha"], w["n_beta"], w["D"], w["bond"]) !=
+                (args.L, args.na, args.nb, args.D, args.bond)):
+            return None
+        return rec["traffic_bytes_per_sigma"]
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def cpu_baseline(args, flops_of):
@@ -277,7 +298,8 @@ def main():
         "gpu_launches": launches,
         "roofline": {"bound": bound, "achieved": round(achieved, 4) if achieved else None,
                      "peak": round(peak, 3), "unit": unit,
-                     "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                     "frac": round(achieved / peak, 4) if achieved else None,
+                     "traffic": measured_traffic(args, prec == B.PREC_MIXED_BF16),
                      "kernel": key, "peak_source": peak_kind,
                      "kernel_ms_per_step": round(kms, 3) if kms else None},
         "profile_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]},
@@ -295,9 +317,28 @@ def main():
             out["cpu_baseline"] = cpu_baseline(args, flops_of)
         except Exception as e:  # pragma: no cover
             out["cpu_baseline"] = {"error": str(e)}
+    d.close()
+    if args.sweeps > 0:
+        # full L->R->L sweeps from the seeded kept-product-state basis, every bond at
+        # dimension D; the phase split follows the paper's Sec. 4.1 categories
+        torch.cuda.synchronize()
+        ds = B.Dmrg(t, v, args.na, args.nb, D=args.D, precision=prec, seed=args.seed, stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        ds.profile_start()
+        energies = ds.sweep(args.sweeps, [args.D] * args.sweeps, tol=args.sweep_tol)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        sprof = ds.profile_stop()
+        out["sweep"] = {"workload": f"{args.sweeps} full sweep(s) L->R->L of L={args.L}, {args.na}a+{args.nb}b, "
+                                    f"D={args.D} at every bond, from the seeded product-state basis, "
+                                    f"Davidson tol {args.sweep_tol:g}",
+                        "seconds_per_sweep": round(ts / args.sweeps, 2),
+                        "phases_s": {k: round(x, 2) for k, x in ds.sweep_phases().items()},
+                        "kernel_s": {k: round(x["ms"] / 1e3, 2) for k, x in sprof.items() if x["launches"]},
+                        "energies": [float(x) for x in energies]}
+        ds.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
-    d.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -157,6 +157,15 @@ dmrg_status dmrg_davidson(dmrg_handle* h, int32_t bond, double* psi_dev, double 
 dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,
                        double* energies);
 
+/* Wall seconds of the last dmrg_sweep call split by phase, in the categories of
+ * the paper's timing breakdown (Sec. 4.1): seconds5[0] Tables (sigma plans and
+ * split operands), [1] Diag_H (Davidson), [2] SVD (density matrices, Jacobi
+ * eigensolver, selection), [3] Ren_l / Ren_r (renormalisation and enlargement of
+ * block operators), [4] StVec (wave function moved to the next bond).  The
+ * stream is synchronised at every phase boundary while a sweep runs, so the
+ * phases add up to the sweep's wall time.  seconds5 is host memory. */
+dmrg_status dmrg_sweep_phases(dmrg_handle* h, double* seconds5);
+
 /* Reduced density matrices at the prepared bond (Sec. 2.2 uses them for
  * orbital rotations): with x = lam_dev, y = psi_dev (device, psi_size doubles)
  *   g1[i*L+j]             += <x| sum_s a+_is a_js |y>

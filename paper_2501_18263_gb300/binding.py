@@ -18,8 +18,9 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOCONV, ERR_NONFINITE, ERR_STAT
 PREC_FP64, PREC_MIXED_BF16 = 0, 1
 
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
-           "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sigma_backward", "dmrg_stats",
+           "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_stats",
            "dmrg_profile", "dmrg_destroy", "dmrg_last_error"]
+SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
 PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "jacobi", "gemm_bf16x", "split", "gemm_bf16x_stage1"]
 
 
@@ -59,6 +60,7 @@ def load_library(path: str | None = None):
         "dmrg_sigma_host_noalloc": ([vp, i32, dp, dp], ctypes.c_int),
         "dmrg_davidson": ([vp, i32, vp, f64, i32, dp, ip], ctypes.c_int),
         "dmrg_sweep": ([vp, i32, ip, f64, dp], ctypes.c_int),
+        "dmrg_sweep_phases": ([vp, dp], ctypes.c_int),
         "dmrg_sigma_backward": ([vp, i32, vp, vp, vp, vp], ctypes.c_int),
         "dmrg_stats": ([vp, i64p], ctypes.c_int),
         "dmrg_profile": ([vp, i32, dp], ctypes.c_int),
@@ -172,6 +174,12 @@ class Dmrg:
                                         Ds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if Ds is not None else None,
                                         float(tol), _dp(e)))
         return e
+
+    def sweep_phases(self):
+        """Wall seconds of the last sweep call per phase (Tables, Diag_H, SVD, Ren, StVec)."""
+        out = np.zeros(5)
+        self._check(self.lib.dmrg_sweep_phases(self.h, _dp(out)))
+        return dict(zip(SWEEP_PHASES, out.tolist()))
 
     def sigma_backward(self, bond, psi_ptr, lam_ptr, g1_ptr, g2_ptr):
         self._check(self.lib.dmrg_sigma_backward(self.h, bond, ctypes.c_void_p(int(psi_ptr)),

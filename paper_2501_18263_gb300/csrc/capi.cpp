@@ -280,6 +280,14 @@ dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedu
   });
 }
 
+dmrg_status dmrg_sweep_phases(dmrg_handle* h, double* seconds5) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !seconds5) return fail(DMRG_ERR_ARG, "bad arguments");
+    for (int k = 0; k < 5; ++k) seconds5[k] = h->eng->phase_s[k];
+    return DMRG_OK;
+  });
+}
+
 dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi, const double* lam,
                                 double* g1, double* g2) {
   return guard([&]() -> dmrg_status {

@@ -173,10 +173,19 @@ class Engine {
   double last_rnorm = 0.0;
   struct StepLog { int sweep, bond, ltr; double energy; int iters; };
   std::vector<StepLog> sweep_log_;
+  // wall seconds of the last run_sweeps call per phase (Sec. 4.1 categories):
+  // 0 Tables (sigma plans), 1 Diag_H (Davidson), 2 SVD (density matrices,
+  // eigensolver, selection), 3 Ren (renormalisation and enlargement), 4 StVec
+  double phase_s[5] = {0, 0, 0, 0, 0};
   void set_D(int D) { P_.D = D; }
+  // phase clock: while a sweep is timed, tick(k) charges the time since the last
+  // tick to phase k (the stream is synchronised at every tick)
+  void tick(int k);
   void set_precision(int p) { P_.precision = p; }
 
  private:
+  bool timing_ = false;
+  double t_last_ = 0.0;
   Problem P_;
   Exec* ex_;
   std::vector<Block> lb_, rb_;

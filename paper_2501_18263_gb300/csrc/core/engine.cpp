@@ -2,6 +2,7 @@
 // eigensolver for the effective Hamiltonian), density-matrix truncation
 // (keep the D largest weights, Sec. 2.1), renormalisation Ren_l / Ren_r and the
 // wave-function transformation StVec of the two-site sweep (Sec. 4.1).
+#include <chrono>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -391,6 +392,7 @@ void Engine::truncate_and_move(bool ltr, int D, double* trunc_w) {
       wo += dims[k];
     }
     ex_->syev(Av, wvv, Zv, nv);
+    tick(2);
   }
   std::vector<double> hw(totw);
   ex_->d2h(hw.data(), wv, totw * sizeof(double));
@@ -487,11 +489,13 @@ void Engine::truncate_and_move(bool ltr, int D, double* trunc_w) {
   }
   // renormalise the operators of the enlarged block that was truncated
   Enlarged Eold = E;
+  tick(2);
   if (ltr) {
     renormalize(true, EL_, EopsL_, iso, lb_[b + 1]);
   } else {
     renormalize(false, ER_, EopsR_, iso, rb_[b + 1]);
   }
+  tick(3);
   Enlarged ELold = EL_, ERold = ER_;
   std::vector<int64_t> old_poff = psi_off_;
   std::vector<int> old_prc = psi_rcoarse_;
@@ -575,6 +579,7 @@ void Engine::truncate_and_move(bool ltr, int D, double* trunc_w) {
   if (psi_cur_) ex_->release(psi_cur_);
   psi_cur_ = npsi;
   psi_cur_cap_ = pn;
+  tick(4);
   prepare_bond(nb);
   if (psi_n_ != pn) throw std::runtime_error("StVec: layout mismatch");
 }
@@ -688,12 +693,24 @@ void Engine::init_sweep_state() {
   ex_->h2d(psi_cur_, h.data(), psi_n_ * sizeof(double));
 }
 
+void Engine::tick(int k) {
+  if (!timing_) return;
+  ex_->sync();
+  const double t = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  phase_s[k] += t - t_last_;
+  t_last_ = t;
+}
+
 std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol) {
   const int L = P_.L;
   if (L < 3) throw std::runtime_error("sweeps need L >= 3");
   if (!psi_cur_ || bond_ != 0) init_sweep_state();
   std::vector<double> E;
   sweep_log_.clear();
+  for (double& x : phase_s) x = 0.0;
+  ex_->sync();
+  t_last_ = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  timing_ = true;
   for (int s = 0; s < nsw; ++s) {
     const int D = Dsched ? Dsched[s] : P_.D;
     double e = 0.0, tw = 0.0;
@@ -702,16 +719,19 @@ std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol) {
     // reported (last step); elsewhere the split-BF16 eigenvector is kept
     for (int b = 0; b <= L - 3; ++b) {   // left to right
       e = davidson(psi_cur_, tol, 100, 24, &iters, 0);
+      tick(1);
       sweep_log_.push_back({s, b, 1, e, iters});
       truncate_and_move(true, D, &tw);
     }
     for (int b = L - 2; b >= 1; --b) {   // right to left
       e = davidson(psi_cur_, tol, 100, 24, &iters, b == 1 ? 1 : 0);
+      tick(1);
       sweep_log_.push_back({s, b, 0, e, iters});
       truncate_and_move(false, D, &tw);
     }
     E.push_back(e);
   }
+  timing_ = false;
   return E;
 }
 

@@ -96,6 +96,7 @@ void Engine::prepare_bond(int bond) {
   free_bond();
   enlarge(true, lb_[bond], bond, EL_, EopsL_);
   enlarge(false, rb_[bond + 2], bond + 1, ER_, EopsR_);
+  tick(3);
   bond_ = bond;
   // psi layout
   QN N{P_.na, P_.nb};
@@ -116,6 +117,7 @@ void Engine::prepare_bond(int bond) {
   psi_n_ = off;
   if (psi_n_ == 0) throw std::runtime_error("prepare_bond: empty two-site space");
   build_sigma_plan();
+  tick(0);
 }
 
 void Engine::build_sigma_plan() {
