@@ -51,8 +51,9 @@ bool finite(const double* p, size_t n) {
 
 // a bounded device-side wait that gave up leaves a nonzero error word
 dmrg_status check_device(dmrg_handle* h) {
-  if (h->eng->problem().precision != 0 && h->eng->exec()->device_error())
-    return fail(DMRG_ERR_TIMEOUT, "a tensor-core pipeline wait gave up; destroy the handle");
+  const int code = h->eng->exec()->device_error();
+  if (code == 9) return fail(DMRG_ERR_NOCONV, "the symmetric eigensolver did not converge");
+  if (code) return fail(DMRG_ERR_TIMEOUT, "a tensor-core pipeline wait gave up; destroy the handle");
   return DMRG_OK;
 }
 

@@ -335,21 +335,231 @@ struct SyevJob {
   int n, pad;
 };
 
-__global__ void __launch_bounds__(256) syev_kernel(const SyevJob* jobs, int* work_i, double* work_d, int maxn) {
+constexpr int SYEV_THREADS = 1024;
+
+// sum over the CTA, returned to every thread (red: >= 33 doubles of shared memory)
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double x = lane < int(blockDim.x >> 5) ? red[lane] : 0.0;
+    x = warp_sum(x);
+    if (lane == 0) red[32] = x;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Symmetric eigen-decomposition A = Z diag(w) Z^T (FP64), the classical route:
+//  1. Householder reduction to tridiagonal form, A = Q T Q^T with
+//     Q = H_0 ... H_{n-3}, H_k = I - tau_k u_k u_k^T (u_k supported on k+1..n-1);
+//  2. Q formed explicitly from the reflectors (backward accumulation);
+//  3. implicit QL iterations with shifts on T (Bowdler, Martin, Reinsch and
+//     Wilkinson, "The QR and QL algorithms for symmetric matrices", Numer. Math.
+//     11 (1968), the tql2 procedure), the plane rotations of every iteration
+//     applied to the columns of Z = Q;
+//  4. eigenvalues sorted ascending, eigenvectors permuted with them.
+// One thread runs the scalar QL recurrences; all threads apply each iteration's
+// rotations to their rows of Z (Z kept column-major while working, so that a
+// rotation of two columns is a coalesced pass).  On non-convergence (more than 60
+// QL iterations for one eigenvalue) *err receives 9.
+__global__ void __launch_bounds__(SYEV_THREADS) syev_kernel(const SyevJob* jobs, int* err, double* work_d,
+                                                           int maxn) {
   const SyevJob jb = jobs[blockIdx.x];
   const int n = jb.n;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   extern __shared__ double sm[];
-  double* cs = sm;                              // 2 * ceil(n/2)+2
-  double* red = sm + maxn + 4;                  // 65
-  int* pp = reinterpret_cast<int*>(red + 72);
-  int* qq = pp + (maxn / 2 + 2);
-  jacobi_core<false>(jb.A, jb.Z, n, n, cs, pp, qq, red);
-  // sort ascending: rank of each diagonal element; permuted columns go through A
+  double* vs = sm;             // Householder vector of the current step
+  double* ps = vs + maxn;      // p = tau A22 v, then w
+  double* dd = ps + maxn;      // diagonal of T, then eigenvalues
+  double* ee = dd + maxn;      // off-diagonal of T (ee[i] couples i and i + 1)
+  double* tt = ee + maxn;      // tau_k
+  double* rc = tt + maxn;      // rotation cosines of one QL iteration
+  double* rs = rc + maxn;      // rotation sines
+  double* red = rs + maxn;     // 40 doubles: reductions and scalars
+  int* ri = reinterpret_cast<int*>(red + 40);   // rotation column indices
+  double* A = jb.A;
+  double* Zc = jb.Z;           // column-major working copy: Zc[c * n + r]
+
+  // ---- 1. tridiagonalisation
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double* x = A + int64_t(k) * n + k + 1;          // row k right of the diagonal (= column k below it)
+    double part = 0.0;
+    for (int i = 1 + tid; i < m; i += nt) part += x[i] * x[i];
+    const double sigma = block_sum(part, red);
+    if (tid == 0) {
+      const double alpha = x[0];
+      dd[k] = A[int64_t(k) * n + k];
+      if (sigma == 0.0) {
+        tt[k] = 0.0;
+        ee[k] = alpha;
+        red[34] = 0.0;
+      } else {
+        const double mu = sqrt(alpha * alpha + sigma);
+        const double beta = alpha <= 0.0 ? mu : -mu;
+        tt[k] = (beta - alpha) / beta;
+        ee[k] = beta;
+        red[34] = 1.0 / (alpha - beta);
+      }
+    }
+    __syncthreads();
+    const double tau = tt[k], scale = red[34];
+    if (tau == 0.0) {
+      if (tid == 0) x[0] = 1.0;
+      __syncthreads();
+      continue;
+    }
+    for (int i = tid; i < m; i += nt) {
+      const double v = i == 0 ? 1.0 : x[i] * scale;
+      vs[i] = v;
+      x[i] = v;   // the reflector is kept in row k for step 2
+    }
+    __syncthreads();
+    // p = tau A22 v: one warp per row, lanes along the row
+    double* A22 = A + int64_t(k + 1) * n + k + 1;
+    for (int r = wid; r < m; r += nw) {
+      const double* row = A22 + int64_t(r) * n;
+      double acc = 0.0;
+      for (int j = lane; j < m; j += 32) acc += row[j] * vs[j];
+      acc = warp_sum(acc);
+      if (lane == 0) ps[r] = tau * acc;
+    }
+    __syncthreads();
+    double pv = 0.0;
+    for (int i = tid; i < m; i += nt) pv += ps[i] * vs[i];
+    const double K = 0.5 * tau * block_sum(pv, red);
+    for (int i = tid; i < m; i += nt) ps[i] -= K * vs[i];   // w
+    __syncthreads();
+    // A22 -= v w^T + w v^T
+    for (int r = wid; r < m; r += nw) {
+      double* row = A22 + int64_t(r) * n;
+      const double vr = vs[r], wr = ps[r];
+      for (int j = lane; j < m; j += 32) row[j] -= vr * ps[j] + wr * vs[j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      dd[n - 2] = A[int64_t(n - 2) * n + n - 2];
+      ee[n - 2] = A[int64_t(n - 2) * n + n - 1];
+    }
+    dd[n - 1] = A[int64_t(n - 1) * n + n - 1];
+    ee[n - 1] = 0.0;
+  }
+  // ---- 2. Q = H_0 ... H_{n-3}, accumulated backwards into Zc
+  for (int64_t e = tid; e < int64_t(n) * n; e += nt) Zc[e] = (e / n == e % n) ? 1.0 : 0.0;
   __syncthreads();
-  double* dg = reinterpret_cast<double*>(work_d) + int64_t(blockIdx.x) * maxn;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = jb.A[i * n + i];
+  for (int k = n - 3; k >= 0; --k) {
+    const double tau = tt[k];
+    if (tau == 0.0) continue;
+    const int m = n - k - 1;
+    const double* u = A + int64_t(k) * n + k + 1;
+    for (int i = tid; i < m; i += nt) vs[i] = u[i];
+    __syncthreads();
+    // y_j = sum_i u_i Q22[i, j] (column j of Q22 contiguous), then Q22 -= tau u y^T
+    for (int j = wid; j < m; j += nw) {
+      double* col = Zc + int64_t(k + 1 + j) * n + k + 1;
+      double acc = 0.0;
+      for (int i = lane; i < m; i += 32) acc += vs[i] * col[i];
+      acc = tau * warp_sum(acc);
+      for (int i = lane; i < m; i += 32) col[i] -= acc * vs[i];
+    }
+    __syncthreads();
+  }
+  // ---- 3. implicit QL on (dd, ee), rotations applied to the columns of Zc
+  // a coupling is negligible relative to its neighbours or to the norm of T (the
+  // second test deflates the rounding-level couplings of a numerically singular
+  // block, e.g. the null space of a density matrix; backward stable either way)
+  const double eps = 2.220446049250313e-16;
+  int l = 0, iter = 0;   // used by thread 0 only
+  double tnorm = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < n; ++i) tnorm = fmax(tnorm, fabs(dd[i]) + fabs(ee[i]) + (i ? fabs(ee[i - 1]) : 0.0));
+  int* ctl = ri + maxn;
+  for (;;) {
+    if (tid == 0) {
+      int nrot = -1;
+      while (l < n) {
+        int mm = l;
+        for (; mm < n - 1; ++mm)
+          if (fabs(ee[mm]) <= eps * (fabs(dd[mm]) + fabs(dd[mm + 1])) || fabs(ee[mm]) <= eps * tnorm) break;
+        if (mm == l) {
+          ++l;
+          iter = 0;
+          continue;
+        }
+        if (++iter > 60) {
+          atomicExch(err, 9);
+          l = n;
+          break;
+        }
+        double g = (dd[l + 1] - dd[l]) / (2.0 * ee[l]);
+        double r = hypot(g, 1.0);
+        g = dd[mm] - dd[l] + ee[l] / (g + (g >= 0.0 ? r : -r));
+        double s = 1.0, c = 1.0, p = 0.0;
+        bool split = false;
+        nrot = 0;
+        for (int i = mm - 1; i >= l; --i) {
+          const double f = s * ee[i], b = c * ee[i];
+          r = hypot(f, g);
+          ee[i + 1] = r;
+          if (r == 0.0) {   // the block splits: restart on the smaller one
+            dd[i + 1] -= p;
+            ee[mm] = 0.0;
+            split = true;
+            break;
+          }
+          s = f / r;
+          c = g / r;
+          g = dd[i + 1] - p;
+          r = (dd[i] - g) * s + 2.0 * c * b;
+          p = s * r;
+          dd[i + 1] = g + p;
+          g = c * r - b;
+          rc[nrot] = c;
+          rs[nrot] = s;
+          ri[nrot] = i;
+          ++nrot;
+        }
+        if (!split) {
+          dd[l] -= p;
+          ee[l] = g;
+          ee[mm] = 0.0;
+        }
+        break;
+      }
+      ctl[0] = (l < n) ? nrot : -1;
+    }
+    __syncthreads();
+    const int nrot = ctl[0];
+    if (nrot < 0) break;
+    if (nrot > 0) {
+      // rotation q mixes columns i = ri[q] and i + 1; they come in descending i, so
+      // column i + 1 of rotation q is column i of rotation q - 1
+      for (int r = tid; r < n; r += nt) {
+        int i = ri[0];
+        double zi1 = Zc[int64_t(i + 1) * n + r];
+        for (int q = 0; q < nrot; ++q) {
+          i = ri[q];
+          const double c = rc[q], s = rs[q];
+          const double zi = Zc[int64_t(i) * n + r];
+          Zc[int64_t(i + 1) * n + r] = s * zi + c * zi1;
+          zi1 = c * zi - s * zi1;
+        }
+        Zc[int64_t(i) * n + r] = zi1;
+      }
+    }
+    __syncthreads();
+  }
+  // ---- 4. sort ascending (rank of each eigenvalue); permuted columns go through A
+  double* dg = work_d + int64_t(blockIdx.x) * maxn;
+  for (int i = tid; i < n; i += nt) dg[i] = dd[i];
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = tid; i < n; i += nt) {
     int r = 0;
     const double di = dg[i];
     for (int j = 0; j < n; ++j) {
@@ -357,11 +567,10 @@ __global__ void __launch_bounds__(256) syev_kernel(const SyevJob* jobs, int* wor
       r += (dj < di) || (dj == di && j < i);
     }
     jb.w[r] = di;
-    for (int row = 0; row < n; ++row) jb.A[row * n + r] = jb.Z[row * n + i];
+    for (int row = 0; row < n; ++row) A[int64_t(row) * n + r] = Zc[int64_t(i) * n + row];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) jb.Z[e] = jb.A[e];
-  (void)work_i;
+  for (int64_t e = tid; e < int64_t(n) * n; e += nt) jb.Z[e] = A[e];
 }
 
 // Rayleigh-Ritz of the Davidson subspace: lowest eigenpair of an m x m matrix (m <= 40)
@@ -761,9 +970,10 @@ class CudaExec : public Exec {
     }
     SyevJob* dj = upload(jobs);
     double* wd = static_cast<double*>(alloc(sizeof(double) * size_t(maxn) * jobs.size()));
-    size_t smem = sizeof(double) * (maxn + 4 + 72) + sizeof(int) * 2 * (maxn / 2 + 2);
+    size_t smem = sizeof(double) * (7 * size_t(maxn) + 40) + sizeof(int) * (size_t(maxn) + 4);
+    if (smem > 227 * 1024) throw std::runtime_error("syev: matrix too large for the shared-memory workspace");
     if (smem > 48 * 1024) CK(cudaFuncSetAttribute(syev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    launch(PROF_EIG, [&] { syev_kernel<<<unsigned(jobs.size()), 256, smem, st_>>>(dj, nullptr, wd, maxn); });
+    launch(PROF_EIG, [&] { syev_kernel<<<unsigned(jobs.size()), SYEV_THREADS, smem, st_>>>(dj, err_, wd, maxn); });
     release(dj);
     release(wd);
   }
