@@ -36,7 +36,7 @@ METRIC = "sigma TFLOP/s & sweep time, L=32 D=2048, mixed vs FP64 at |dE|<=1e-6 E
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--L", type=int, default=32)
@@ -52,6 +52,15 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=0,
                     help="also time this many full two-site sweeps at bond dimension D (fresh seeded basis)")
     ap.add_argument("--sweep-tol", type=float, default=1e-6, help="Davidson residual tolerance of the timed sweeps")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="also time the batched form on this many independent problems (L ~ U[10,20], "
+                         "electrons = L with alpha/beta split within +-2, D in {256,512,1024}, seeds 100..)")
+    ap.add_argument("--compare-davidson", default="",
+                    help="L,na,nb,D: Davidson (Diag_H) at the centre bond of a fixed seeded basis in FP64 and in "
+                         "split-BF16 with FP64 refinement, same start vector; times, energies and |dE|")
+    ap.add_argument("--compare-sweeps", default="",
+                    help="L,na,nb,D,n_sweeps: time n full sweeps in FP64 and in split-BF16 from the same seeded "
+                         "basis and report both sweep times and |dE| (mixed vs FP64)")
     a = ap.parse_args()
     a.na = a.L // 2 if a.na is None else a.na
     a.nb = a.L // 2 if a.nb is None else a.nb
@@ -82,7 +91,7 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -134,6 +143,23 @@ def measured_traffic(args, mixed):
         return rec["traffic_bytes_per_sigma"]
     except (OSError, KeyError, ValueError):
         return None
+
+
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks of the job (every rank gets it)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_tflops(flops_per_rank, world, ms):
+    """Whole-job rate: every rank runs an independent replica of the same workload,
+    so the job does world x flops_per_rank in the slowest rank's time ms."""
+    return flops_per_rank * world / (ms * 1e-3) / 1e12
 
 
 def cpu_baseline(args, flops_of):
@@ -212,12 +238,8 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = flops * world / (ms * 1e-3) / 1e12
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    value = job_tflops(flops, world, ms)
 
     # the FP64 path on the same handle and operators, timed beside the mixed one
     fp64 = None
@@ -246,11 +268,7 @@ def main():
     ke = max(1, args.steps)
     for _ in range(ke):
         d.sigma_host(args.bond, psi_h)
-    e2e_s = (time.perf_counter() - t0) / ke
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / ke, world, dev)
 
     pk, pk_kind = peaks()
     if prec == B.PREC_FP64:
@@ -293,7 +311,7 @@ def main():
                                         "mix_plane_bytes", "gemm_problems", "gemm_segments")},
         },
         "clocks": clocks,
-        "e2e": {"value": round(flops / e2e_s / 1e12, 4), "unit": "TFLOP/s",
+        "e2e": {"value": round(job_tflops(flops, world, e2e_s * 1e3), 4), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": launches,
         "roofline": {"bound": bound, "achieved": round(achieved, 4) if achieved else None,
@@ -337,10 +355,155 @@ def main():
                         "kernel_s": {k: round(x["ms"] / 1e3, 2) for k, x in sprof.items() if x["launches"]},
                         "energies": [float(x) for x in energies]}
         ds.close()
+    if args.compare_davidson:
+        out["davidson_compare"] = compare_davidson(args, B, I, stream)
+    if args.compare_sweeps:
+        out["sweep_compare"] = compare_sweeps(args, B, I, stream)
+    if args.batched > 0:
+        out["batched"] = batched_bench(args, B, I)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def compare_davidson(args, B, I, stream):
+    """Diag_H of one bond in FP64 and in split-BF16 (with its FP64 residual refinement) on the same
+    seeded basis and start vector: wall seconds, iterations, energies and |dE|."""
+    import torch
+    L, na, nb, D = (int(x) for x in args.compare_davidson.split(","))
+    bond = L // 2 - 1
+    t, v = I.synthetic_integrals(L, args.seed)
+    bp = I.bond_problem(L, na, nb, D, bond, seed=args.seed + 1)
+    res = {"workload": f"Davidson at the centre bond (k={bond}) of L={L}, {na}a+{nb}b, D={D}, fixed seeded basis "
+                       f"and start vector, residual tol {args.sweep_tol:g}"}
+    for name, prec in (("fp64", B.PREC_FP64), ("mixed", B.PREC_MIXED_BF16)):
+        d = B.Dmrg(t, v, na, nb, D=D, precision=prec, seed=args.seed, stream=stream.cuda_stream)
+        d.load_bond_problem(bp)
+        d.prepare(bond)
+        x = torch.tensor(B.pack_psi(bp.psi), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e, it = d.davidson(bond, x.data_ptr(), tol=args.sweep_tol, max_iter=400)
+        torch.cuda.synchronize()
+        res[name] = {"seconds": round(time.perf_counter() - t0, 3), "iterations": it, "energy": e}
+        d.close()
+    res["abs_dE"] = abs(res["fp64"]["energy"] - res["mixed"]["energy"])
+    res["speedup_mixed_vs_fp64"] = round(res["fp64"]["seconds"] / res["mixed"]["seconds"], 3)
+    return res
+
+
+def compare_sweeps(args, B, I, stream):
+    """Full sweeps of one problem in FP64 and in split-BF16 from the same seeded basis:
+    wall seconds per sweep (with the Sec. 4.1 phase split) and the energy difference."""
+    import torch
+    L, na, nb, D, ns = (int(x) for x in args.compare_sweeps.split(","))
+    t, v = I.synthetic_integrals(L, args.seed)
+    res = {"workload": f"{ns} full sweep(s) L->R->L of L={L}, {na}a+{nb}b, D={D} at every bond, synthetic "
+                       f"integrals seed {args.seed}, same seeded product-state basis for both precisions, "
+                       f"Davidson tol {args.sweep_tol:g}"}
+    for name, prec in (("fp64", B.PREC_FP64), ("mixed", B.PREC_MIXED_BF16)):
+        torch.cuda.synchronize()
+        d = B.Dmrg(t, v, na, nb, D=D, precision=prec, seed=args.seed, stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        e = d.sweep(ns, [D] * ns, tol=args.sweep_tol)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        res[name] = {"seconds_per_sweep": round(ts / ns, 2), "energies": [float(x) for x in e],
+                     "phases_s_all_sweeps": {k: round(x, 2) for k, x in d.sweep_phases().items()}}
+        d.close()
+    ef, em = res["fp64"]["energies"], res["mixed"]["energies"]
+    res["abs_dE_per_sweep"] = [abs(a - b) for a, b in zip(ef, em)]
+    res["speedup_mixed_vs_fp64"] = round(res["fp64"]["seconds_per_sweep"] / res["mixed"]["seconds_per_sweep"], 3)
+    return res
+
+
+def batched_problem(i):
+    """Problem i of the batched workload (seed 100 + i)."""
+    seed = 100 + i
+    rng = np.random.default_rng(seed)
+    L = int(rng.integers(10, 21))
+    splits = [s for s in range(-2, 3) if (s - L) % 2 == 0]
+    s = int(rng.choice(splits))
+    D = int(rng.choice([256, 512, 1024]))
+    return L, (L + s) // 2, (L - s) // 2, D, seed
+
+
+def batched_bench(args, B, I):
+    """Split-BF16 sigma steps of many independent problems (each at its centre bond):
+    one by one through dmrg_sigma, batched in shared grouped launches, and batched
+    from a captured CUDA graph; problems/s = sigma steps of all problems per second."""
+    import torch
+    stream = torch.cuda.Stream()
+    ds, bonds, psis, sigs, flops, meta = [], [], [], [], 0, []
+    for i in range(args.batched):
+        L, na, nb, D, seed = batched_problem(i)
+        bond = L // 2 - 1
+        t, v = I.synthetic_integrals(L, seed)
+        bp = I.bond_problem(L, na, nb, D, bond, seed=seed + 1000)
+        try:
+            d = B.Dmrg(t, v, na, nb, D=D, precision=B.PREC_MIXED_BF16, seed=seed, stream=stream.cuda_stream)
+            d.load_bond_problem(bp)
+            d.prepare(bond)
+        except B.DmrgError as e:
+            if e.status != B.ERR_OOM:
+                raise
+            break
+        st = d.stats()
+        flops += st["flops_stage1"] + st["flops_stage2"]
+        x = B.pack_psi(bp.psi)
+        psis.append(torch.tensor(x / np.linalg.norm(x), dtype=torch.float64, device="cuda"))
+        sigs.append(torch.empty_like(psis[-1]))
+        ds.append(d)
+        bonds.append(bond)
+        meta.append((L, na, nb, D))
+    torch.cuda.synchronize()
+    n = len(ds)
+    pp = [p.data_ptr() for p in psis]
+    sp = [s.data_ptr() for s in sigs]
+    batch = B.Batch(ds, bonds)
+
+    def timed(fn, k):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / k
+
+    def one_by_one():
+        for d, b, p, s in zip(ds, bonds, pp, sp):
+            d.sigma(b, p, s)
+
+    k = max(3, args.steps // 3)
+    t_seq = timed(one_by_one, k)
+    t_eager = timed(lambda: batch.sigma(pp, sp, graph=False), k)
+    t_graph = timed(lambda: batch.sigma(pp, sp, graph=True), k)
+    # per-problem energy-scale error of the batched split-BF16 sigma against FP64:
+    # |<psi|sigma_mixed> - <psi|sigma_fp64>| with psi normalised
+    batch.sigma(pp, sp, graph=True)
+    torch.cuda.synchronize()
+    e_mix = [float((p * s).sum()) for p, s in zip(psis, sigs)]
+    de = []
+    for d, b, x, s, em in zip(ds, bonds, psis, sigs, e_mix):
+        d.sigma_ex(b, x.data_ptr(), s.data_ptr(), B.PREC_FP64)
+        de.append(abs(em - float((x * s).sum())))
+    batch.close()
+    for d in ds:
+        d.close()
+    return {"workload": f"{n} independent problems, problem i: seed 100+i, L ~ U[10,20], electrons = L with "
+                        f"alpha-beta in {{-2..2}}, D in {{256,512,1024}}, centre bond, synthetic integrals",
+            "problems": n, "flops_per_step": flops,
+            "problems_per_s": {"one_by_one": round(n / t_seq, 1), "batched": round(n / t_eager, 1),
+                               "batched_graph": round(n / t_graph, 1)},
+            "tflops": {"one_by_one": round(flops / t_seq / 1e12, 3), "batched": round(flops / t_eager / 1e12, 3),
+                       "batched_graph": round(flops / t_graph / 1e12, 3)},
+            "ms_per_step": {"one_by_one": round(t_seq * 1e3, 3), "batched": round(t_eager * 1e3, 3),
+                            "batched_graph": round(t_graph * 1e3, 3)},
+            "abs_dE_mixed_vs_fp64": {"max": max(de), "median": float(np.median(de))},
+            "L_D": [[m[0], m[3]] for m in meta]}
 
 
 def run_reference(args, rank, world):

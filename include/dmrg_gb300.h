@@ -171,7 +171,10 @@ dmrg_status dmrg_sweep_phases(dmrg_handle* h, double* seconds5);
  *   g1[i*L+j]             += <x| sum_s a+_is a_js |y>
  *   g2[((i*L+j)*L+k)*L+l] += <x| sum_st a+_is a+_kt a_lt a_js |y>
  * so that dE/dt = g1 and dE/dv = g2/2 for x = y = the normalised eigenvector.
- * g1, g2 are device buffers (L^2 and L^4 doubles). */
+ * g1, g2 are device buffers (L^2 and L^4 doubles).
+ * NOT BUILT in this version: the call checks its arguments and the bond
+ * index, then returns DMRG_ERR_ARG with the message "dmrg_sigma_backward: not
+ * available in this build"; it prepares nothing and writes nothing. */
 dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi_dev, const double* lam_dev,
                                 double* g1_dev, double* g2_dev);
 
@@ -190,6 +193,33 @@ dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out16);
  * pack / reduce, 6 split-BF16 tensor-core GEMM of sigma stage 1.
  * out14 may be NULL when mode = 1. */
 dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out14);
+
+/*
+ * Batched form (many independent problems; the grouped launch of the sigma
+ * GEMMs over the block-sparse tasks of Sec. 2.4, item (c), taken across
+ * problems): the split-BF16 sigma steps of n problems, each a handle prepared at
+ * its bond, run as one grouped tensor-core launch per stage whose tiles are
+ * sorted together by work, so that problems too small to fill the GPU alone
+ * fill it together.  Each problem's result is bit-identical to dmrg_sigma on
+ * its handle.
+ *   dmrg_batch_create: handles[i] (created with DMRG_PREC_MIXED_BF16, all on
+ *     one device and one stream, each appearing once) must be prepared at
+ *     bonds[i] (host int32[n]).  The batch copies the handles' plans into one
+ *     merged plan owned by the first handle; the handles must stay alive and
+ *     prepared at those bonds while the batch lives (a handle prepared again
+ *     makes dmrg_batch_sigma return DMRG_ERR_STATE).  Destroy the batch before
+ *     its handles.
+ *   dmrg_batch_sigma: psi_dev[i], sigma_dev[i] (host arrays of n device
+ *     pointers, psi_size doubles of problem i each).  use_graph = 1 captures the
+ *     whole step into a CUDA graph on the first call (and whenever the buffer
+ *     pointers change) and replays it; it needs a created, non-default stream
+ *     and kernel timing off.  The call waits for the step to finish.
+ */
+typedef struct dmrg_batch dmrg_batch;
+dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int32_t* bonds, dmrg_batch** out);
+dmrg_status dmrg_batch_sigma(dmrg_batch* b, const double* const* psi_dev, double* const* sigma_dev,
+                             int32_t use_graph);
+void dmrg_batch_destroy(dmrg_batch* b);
 
 void dmrg_destroy(dmrg_handle* h);
 

@@ -19,7 +19,8 @@ PREC_FP64, PREC_MIXED_BF16 = 0, 1
 
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
            "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_stats",
-           "dmrg_profile", "dmrg_destroy", "dmrg_last_error"]
+           "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_destroy", "dmrg_destroy",
+           "dmrg_last_error"]
 SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
 PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "jacobi", "gemm_bf16x", "split", "gemm_bf16x_stage1"]
 
@@ -64,6 +65,9 @@ def load_library(path: str | None = None):
         "dmrg_sigma_backward": ([vp, i32, vp, vp, vp, vp], ctypes.c_int),
         "dmrg_stats": ([vp, i64p], ctypes.c_int),
         "dmrg_profile": ([vp, i32, dp], ctypes.c_int),
+        "dmrg_batch_create": ([i32, ctypes.POINTER(vp), ip, ctypes.POINTER(vp)], ctypes.c_int),
+        "dmrg_batch_sigma": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32], ctypes.c_int),
+        "dmrg_batch_destroy": ([vp], None),
         "dmrg_destroy": ([vp], None),
         "dmrg_last_error": ([], ctypes.c_char_p),
     }
@@ -201,6 +205,38 @@ class Dmrg:
                 "gemm_segments", "launches_per_sigma", "mix_tiles1", "mix_steps1", "mix_tiles2", "mix_steps2",
                 "mix_x_elems", "mix_plane_bytes"]
         return dict(zip(keys, (int(x) for x in o)))
+
+
+class Batch:
+    """Split-BF16 sigma steps of several prepared problems in shared grouped launches."""
+
+    def __init__(self, problems, bonds):
+        self.problems = list(problems)   # keeps the handles alive while the batch lives
+        self.lib = self.problems[0].lib
+        n = len(self.problems)
+        hs = (ctypes.c_void_p * n)(*[p.h.value for p in self.problems])
+        bs = np.ascontiguousarray(bonds, dtype=np.int32)
+        b = ctypes.c_void_p()
+        self._check(self.lib.dmrg_batch_create(n, hs, bs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                               ctypes.byref(b)))
+        self.b = b
+
+    def _check(self, st):
+        if st != OK:
+            raise DmrgError(st, self.lib.dmrg_last_error().decode())
+
+    def sigma(self, psi_ptrs, sig_ptrs, graph=False):
+        n = len(self.problems)
+        ps = (ctypes.c_void_p * n)(*[int(x) for x in psi_ptrs])
+        ss = (ctypes.c_void_p * n)(*[int(x) for x in sig_ptrs])
+        self._check(self.lib.dmrg_batch_sigma(self.b, ps, ss, 1 if graph else 0))
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.dmrg_batch_destroy(self.b)
+            self.b = None
+
+    __del__ = close
 
 
 def pack_psi(blocks):

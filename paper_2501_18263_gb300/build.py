@@ -31,7 +31,7 @@ def _nvcc():
 
 
 def _sources():
-    cpp = sorted(glob.glob(os.path.join(CSRC, "core", "*.cpp"))) + [os.path.join(CSRC, "capi.cpp")]
+    cpp = sorted(glob.glob(os.path.join(CSRC, "core", "*.cpp"))) + sorted(glob.glob(os.path.join(CSRC, "*.cpp")))
     cu = sorted(glob.glob(os.path.join(CSRC, "kernels", "*.cu")))
     return cpp, cu
 

@@ -1,0 +1,223 @@
+// Batched form of the sigma step: many independent problems (handles prepared
+// at their bonds) share one grouped tensor-core launch per stage, and the whole
+// step can be captured once into a CUDA graph and replayed.
+//
+// The split-BF16 sigma of one problem is: psi -> split planes, local term H_L',
+// stage 1 (X_nu = O_L psi), stage 2 (sigma = sum_nu X_nu O_R^T, split-K parts),
+// fixed-order reduction of the parts, double-float -> FP64.  The two stages and
+// the local term are grouped GEMMs over a tile list; their plans hold absolute
+// device addresses, so the plans of several problems concatenate into one list
+// whose tiles, sorted together by work, keep every SM busy even when each
+// problem alone is too small to fill the GPU.  Each output tile is computed
+// exactly as in the single-problem launch, so the batched sigma equals the
+// per-problem sigma bit for bit.
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/dmrg_gb300.h"
+#include "capi_internal.h"
+#include "exec_errors.h"
+
+struct dmrg_batch {
+  std::vector<dmrg_handle*> h;
+  std::vector<int> bond;
+  std::vector<uint64_t> gen;
+  dmrg::Exec* owner = nullptr;   // executor of the first handle: holds the merged plans
+  cudaStream_t st = nullptr;
+  int plan_hl = -1, plan1 = -1, plan2 = -1;
+  // captured graph and the buffers it was captured with
+  std::vector<const double*> g_psi;
+  std::vector<double*> g_sig;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+dmrg_status fail(dmrg_status s, const std::string& m) {
+  dmrg_internal_set_error(m.c_str());
+  return s;
+}
+
+template <class F>
+dmrg_status guard(F&& f) {
+  try {
+    dmrg_internal_set_error("");
+    return f();
+  } catch (const dmrg::CudaError& e) {
+    return fail(DMRG_ERR_CUDA, e.what());
+  } catch (const dmrg::OomError& e) {
+    return fail(DMRG_ERR_OOM, e.what());
+  } catch (const dmrg::TimeoutError& e) {
+    return fail(DMRG_ERR_TIMEOUT, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(DMRG_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(DMRG_ERR_ARG, e.what());
+  } catch (...) {
+    return fail(DMRG_ERR_STATE, "unknown error");
+  }
+}
+
+// one plan in the owner's executor made of the given plans of several executors
+int merge_plans(dmrg::Exec* owner, const std::vector<std::pair<dmrg::Exec*, int>>& parts) {
+  std::vector<dmrg::MixProb> P;
+  std::vector<dmrg::MixSeg> S;
+  std::vector<int64_t> bcol, ccol;
+  std::vector<float> acol;
+  for (const auto& pr : parts) {
+    if (pr.second < 0) continue;
+    const dmrg::Exec::MixPlanHost& H = pr.first->mix_plan_host(pr.second);
+    // a gathered 8-row unit has two bcol entries and eight ccol / acol entries
+    if (H.bcol.size() * 4 != H.ccol.size() || H.acol.size() != H.ccol.size())
+      throw std::runtime_error("batch: gathered-row tables of a plan are inconsistent");
+    const int so = int(S.size());
+    const int64_t co = int64_t(ccol.size());
+    for (dmrg::MixProb q : H.p) {
+      q.s0 += so;
+      q.s1 += so;
+      if (q.mode == 3) q.cm0 += co;
+      P.push_back(q);
+    }
+    S.insert(S.end(), H.s.begin(), H.s.end());
+    bcol.insert(bcol.end(), H.bcol.begin(), H.bcol.end());
+    ccol.insert(ccol.end(), H.ccol.begin(), H.ccol.end());
+    acol.insert(acol.end(), H.acol.begin(), H.acol.end());
+  }
+  if (P.empty()) return -1;
+  return owner->mix_plan_g(P, S, bcol, ccol, acol);
+}
+
+void free_graph(dmrg_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->g_psi.clear();
+  b->g_sig.clear();
+}
+
+// the batched step, issued on the shared stream (no allocation, no host wait)
+void issue(dmrg_batch* b, const double* const* psi, double* const* sig) {
+  for (size_t i = 0; i < b->h.size(); ++i) b->h[i]->eng->batch_prologue(psi[i]);
+  if (b->plan_hl >= 0) b->owner->mix_run(b->plan_hl);
+  if (b->plan1 >= 0) b->owner->mix_run(b->plan1);
+  for (size_t i = 0; i < b->h.size(); ++i) b->h[i]->eng->batch_zero_parts();
+  if (b->plan2 >= 0) b->owner->mix_run(b->plan2);
+  for (size_t i = 0; i < b->h.size(); ++i) b->h[i]->eng->batch_epilogue(sig[i]);
+}
+
+}  // namespace
+
+extern "C" {
+
+dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int32_t* bonds, dmrg_batch** out) {
+  return guard([&]() -> dmrg_status {
+    if (!out || n <= 0 || !handles || !bonds) return fail(DMRG_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    auto b = std::make_unique<dmrg_batch>();
+    for (int i = 0; i < n; ++i) {
+      dmrg_handle* h = handles[i];
+      if (!h) return fail(DMRG_ERR_ARG, "null handle");
+      for (int j = 0; j < i; ++j)
+        if (handles[j] == h) return fail(DMRG_ERR_ARG, "a handle appears twice in the batch");
+      if (h->eng->problem().precision != DMRG_PREC_MIXED_BF16)
+        return fail(DMRG_ERR_ARG, "batched sigma needs handles created with DMRG_PREC_MIXED_BF16");
+      if (h->eng->bond() != bonds[i]) return fail(DMRG_ERR_ARG, "handle " + std::to_string(i) + " is not prepared at its bond");
+      if (!h->eng->batchable())
+        return fail(DMRG_ERR_ARG, "handle " + std::to_string(i) + " splits its terms into several chunks (memory cap)");
+      if (h->device != handles[0]->device) return fail(DMRG_ERR_ARG, "handles on different devices");
+      if (h->eng->exec()->stream() != handles[0]->eng->exec()->stream())
+        return fail(DMRG_ERR_ARG, "handles must share one CUDA stream");
+      b->h.push_back(h);
+      b->bond.push_back(bonds[i]);
+      b->gen.push_back(h->eng->plan_generation());
+    }
+    b->owner = handles[0]->eng->exec();
+    b->st = static_cast<cudaStream_t>(b->owner->stream());
+    std::vector<std::pair<dmrg::Exec*, int>> hl, p1, p2;
+    for (dmrg_handle* h : b->h) {
+      hl.push_back({h->eng->exec(), h->eng->mix_plan_hl()});
+      p1.push_back({h->eng->exec(), h->eng->mix_plan1()});
+      p2.push_back({h->eng->exec(), h->eng->mix_plan2()});
+    }
+    b->plan_hl = merge_plans(b->owner, hl);
+    b->plan1 = merge_plans(b->owner, p1);
+    b->plan2 = merge_plans(b->owner, p2);
+    b->owner->sync();
+    *out = b.release();
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_batch_sigma(dmrg_batch* b, const double* const* psi_dev, double* const* sigma_dev,
+                             int32_t use_graph) {
+  return guard([&]() -> dmrg_status {
+    if (!b || !psi_dev || !sigma_dev) return fail(DMRG_ERR_ARG, "null argument");
+    const size_t n = b->h.size();
+    for (size_t i = 0; i < n; ++i) {
+      if (!psi_dev[i] || !sigma_dev[i]) return fail(DMRG_ERR_ARG, "null buffer");
+      if (b->h[i]->eng->bond() != b->bond[i] || b->h[i]->eng->plan_generation() != b->gen[i])
+        return fail(DMRG_ERR_STATE, "a handle of the batch was prepared again; destroy and recreate the batch");
+    }
+    if (use_graph) {
+      if (b->st == nullptr) return fail(DMRG_ERR_ARG, "the graph form needs handles on a created (non-default) stream");
+      for (dmrg_handle* h : b->h)
+        if (h->eng->exec()->profiling()) return fail(DMRG_ERR_ARG, "kernel timing is on; the graph form cannot capture it");
+      bool same = b->gexec != nullptr;
+      for (size_t i = 0; same && i < n; ++i) same = b->g_psi[i] == psi_dev[i] && b->g_sig[i] == sigma_dev[i];
+      if (!same) {
+        free_graph(b);
+        cudaError_t rc = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+        if (rc != cudaSuccess) return fail(DMRG_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(rc));
+        try {
+          issue(b, psi_dev, sigma_dev);
+        } catch (...) {
+          cudaGraph_t g = nullptr;
+          cudaStreamEndCapture(b->st, &g);
+          if (g) cudaGraphDestroy(g);
+          cudaGetLastError();
+          throw;
+        }
+        rc = cudaStreamEndCapture(b->st, &b->graph);
+        if (rc != cudaSuccess) {
+          b->graph = nullptr;
+          return fail(DMRG_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(rc));
+        }
+        rc = cudaGraphInstantiate(&b->gexec, b->graph, 0);
+        if (rc != cudaSuccess) {
+          b->gexec = nullptr;
+          free_graph(b);
+          return fail(DMRG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(rc));
+        }
+        b->g_psi.assign(psi_dev, psi_dev + n);
+        b->g_sig.assign(sigma_dev, sigma_dev + n);
+      }
+      cudaError_t rc = cudaGraphLaunch(b->gexec, b->st);
+      if (rc != cudaSuccess) return fail(DMRG_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(rc));
+    } else {
+      issue(b, psi_dev, sigma_dev);
+    }
+    b->owner->sync();
+    if (b->owner->device_error()) return fail(DMRG_ERR_TIMEOUT, "a tensor-core pipeline wait gave up; destroy the handles");
+    return DMRG_OK;
+  });
+}
+
+void dmrg_batch_destroy(dmrg_batch* b) {
+  if (!b) return;
+  try {
+    free_graph(b);
+    for (int id : {b->plan_hl, b->plan1, b->plan2})
+      if (id >= 0) b->owner->mix_plan_free(id);
+    b->owner->sync();
+  } catch (...) {
+  }
+  delete b;
+}
+
+}  // extern "C"

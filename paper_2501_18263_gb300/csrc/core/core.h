@@ -183,9 +183,23 @@ class Engine {
   void tick(int k);
   void set_precision(int p) { P_.precision = p; }
 
+  // Batched form: the split-BF16 sigma of the prepared bond as separate steps,
+  // so that the tensor-core tiles of several problems can share one grouped
+  // launch per stage.  Valid while batchable() (one term chunk); the plan ids
+  // are the executor's, and plan_generation() changes whenever they are rebuilt.
+  bool batchable() const { return bond_ >= 0 && mixed_ready_ && mchunks_.size() == 1; }
+  int mix_plan_hl() const { return mplan_hl_; }
+  int mix_plan1() const { return mchunks_.empty() ? -1 : mchunks_[0].plan1; }
+  int mix_plan2() const { return mchunks_.empty() ? -1 : mchunks_[0].plan2; }
+  uint64_t plan_generation() const { return plan_gen_; }
+  void batch_prologue(const double* psi);   // psi (device) -> split operand planes
+  void batch_zero_parts();                  // clear the split-K part slots
+  void batch_epilogue(double* sig);         // parts -> FP64 sigma (device)
+
  private:
   bool timing_ = false;
   double t_last_ = 0.0;
+  uint64_t plan_gen_ = 0;
   Problem P_;
   Exec* ex_;
   std::vector<Block> lb_, rb_;

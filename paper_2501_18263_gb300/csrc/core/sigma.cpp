@@ -68,6 +68,7 @@ void Engine::free_bond() {
 }
 
 void Engine::free_mixed() {
+  ++plan_gen_;
   for (auto& c : mchunks_) {
     if (c.plan1 >= 0) ex_->mix_plan_free(c.plan1);
     if (c.plan2 >= 0) ex_->mix_plan_free(c.plan2);
@@ -121,6 +122,7 @@ void Engine::prepare_bond(int bond) {
 }
 
 void Engine::build_sigma_plan() {
+  ++plan_gen_;
   const int L = P_.L;
   const int b = bond_;
   const int nL = 2 * (b + 1);  // spin-orbitals of L'
@@ -898,6 +900,20 @@ void Engine::sigma_precision(const double* psi, double* sig, int precision) {
     ex_->mix_run(mchunks_[c].plan2);
     ex_->reduce_parts(part_, nparts_ + (c == 0 ? 1 : 0), psi_n_, shi_, slo_, c > 0);
   }
+  ex_->df_to_f64(shi_, slo_, sig, psi_n_);
+}
+
+void Engine::batch_prologue(const double* psi) {
+  ex_->d2d(psi_in_, psi, psi_n_ * sizeof(double));
+  ex_->split_run(psi_split_);
+}
+
+void Engine::batch_zero_parts() { ex_->zero(part_, size_t(nparts_) * 2 * psi_n_ * sizeof(float)); }
+
+void Engine::batch_epilogue(double* sig) {
+  // the same fixed-order reduction as the single-problem path (parts and the
+  // local-term slot of the one chunk)
+  ex_->reduce_parts(part_, nparts_ + 1, psi_n_, shi_, slo_, 0);
   ex_->df_to_f64(shi_, slo_, sig, psi_n_);
 }
 

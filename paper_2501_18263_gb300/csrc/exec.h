@@ -162,6 +162,19 @@ class Exec {
                          const std::vector<float>& acol) = 0;
   virtual void mix_run(int plan) = 0;
   virtual void mix_plan_free(int plan) = 0;
+  // host copy of a plan's problems, segments and gathered-row tables (kept so that
+  // plans of several problems can be merged into one grouped launch)
+  struct MixPlanHost {
+    std::vector<MixProb> p;
+    std::vector<MixSeg> s;
+    std::vector<int64_t> bcol, ccol;
+    std::vector<float> acol;
+  };
+  virtual const MixPlanHost& mix_plan_host(int plan) const = 0;
+  // the CUDA stream (cudaStream_t) all work is ordered on, and whether kernel
+  // timing is on (timing records events and drains them with host waits)
+  virtual void* stream() const = 0;
+  virtual bool profiling() const = 0;
   virtual int split_plan(const std::vector<SplitTask>& t) = 0;
   virtual void split_run(int plan) = 0;
   virtual void split_plan_free(int plan) = 0;

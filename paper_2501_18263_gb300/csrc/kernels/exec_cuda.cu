@@ -45,13 +45,18 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmTile* __restric
   const GemmTile tl = tiles[blockIdx.x];
   const GemmProb p = probs[tl.prob];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  // warp w owns rows 16 (w / 2) .. +15 and columns 32 (w % 2) .. +31 of the
+  // tile, its lanes 4 x 8 sub-tiles of 4 x 4; a warp whose rows or columns lie
+  // wholly past a ragged edge skips the multiply-adds (warp-uniform test)
+  const int warp = tid >> 5, lane = tid & 31;
+  const int ty = 4 * (warp >> 1) + (lane >> 3), tx = 8 * (warp & 1) + (lane & 7);
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
   const int Mt = min(TM, p.M - tl.m0), Nt = min(TN, p.N - tl.n0);
+  const bool busy = 16 * (warp >> 1) < Mt && 32 * (warp & 1) < Nt;
   for (int s = p.s0; s < p.s1; ++s) {
     const GemmSeg g = segs[s];
     for (int k0 = 0; k0 < g.K; k0 += TK) {
@@ -77,17 +82,19 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmTile* __restric
         Bs[kb][n] = b;
       }
       __syncthreads();
+      if (busy) {
 #pragma unroll
-      for (int k = 0; k < TK; ++k) {
-        double a[4], b[4];
+        for (int k = 0; k < TK; ++k) {
+          double a[4], b[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+          for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+          for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
       }
       __syncthreads();
     }
@@ -802,6 +809,7 @@ class CudaExec : public Exec {
     int ntiles = 0;
     int cls = PROF_MIXED;
     bool live = false;
+    MixPlanHost host;
   };
   struct SplitPlanD {
     SplitTask* t = nullptr;
@@ -868,6 +876,7 @@ class CudaExec : public Exec {
     pl.acol = upload(acol);
     pl.live = true;
     pl.cls = (!p.empty() && p[0].mode != 0) ? PROF_MIXED1 : PROF_MIXED;
+    pl.host = MixPlanHost{p, s, bcol, ccol, acol};
     for (size_t i = 0; i < mplans_.size(); ++i)
       if (!mplans_[i].live) {
         mplans_[i] = pl;
@@ -882,6 +891,9 @@ class CudaExec : public Exec {
     launch(pl.cls, [&] { launch_mixed_gemm(pl.tiles, pl.ntiles, pl.probs, pl.segs, pl.bcol, pl.ccol, pl.acol, err_, nsm_, st_); });
   }
   void mix_plan_free(int id) override { mix_free(id); }
+  const MixPlanHost& mix_plan_host(int id) const override { return mplans_.at(id).host; }
+  void* stream() const override { return st_; }
+  bool profiling() const override { return prof_; }
   void split_plan_free(int id) override {
     SplitPlanD& pl = splans_.at(id);
     if (!pl.live) return;
@@ -897,6 +909,7 @@ class CudaExec : public Exec {
     cudaFreeAsync(pl.bcol, st_);
     cudaFreeAsync(pl.ccol, st_);
     cudaFreeAsync(pl.acol, st_);
+    pl.host = MixPlanHost{};
     pl.live = false;
   }
   int split_plan(const std::vector<SplitTask>& t) override {

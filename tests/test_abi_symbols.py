@@ -53,3 +53,16 @@ def test_argument_errors_without_a_device(lib):
     assert L.dmrg_sigma(None, 0, None, None) == binding.ERR_ARG
     L.dmrg_destroy(None)
 
+
+
+def test_batch_argument_errors_without_a_device(lib):
+    from paper_2501_18263_gb300 import binding
+    L = binding.load_library(lib)
+    b = ctypes.c_void_p()
+    assert L.dmrg_batch_create(0, None, None, ctypes.byref(b)) == binding.ERR_ARG
+    hs = (ctypes.c_void_p * 1)(None)
+    bonds = (ctypes.c_int32 * 1)(0)
+    assert L.dmrg_batch_create(1, hs, bonds, ctypes.byref(b)) == binding.ERR_ARG
+    assert b"null handle" in L.dmrg_last_error()
+    assert L.dmrg_batch_sigma(None, None, None, 0) == binding.ERR_ARG
+    L.dmrg_batch_destroy(None)
