@@ -205,10 +205,11 @@ dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out14);
  *   dmrg_batch_create: handles[i] (created with DMRG_PREC_MIXED_BF16, all on
  *     one device and one stream, each appearing once) must be prepared at
  *     bonds[i] (host int32[n]).  The batch copies the handles' plans into one
- *     merged plan owned by the first handle; the handles must stay alive and
- *     prepared at those bonds while the batch lives (a handle prepared again
- *     makes dmrg_batch_sigma return DMRG_ERR_STATE).  Destroy the batch before
- *     its handles.
+ *     merged plan owned by the first handle.  The handles must stay prepared at
+ *     those bonds while the batch is used: after dmrg_prepare on one of them
+ *     (even at the same bond) or dmrg_destroy of one of them, dmrg_batch_sigma
+ *     returns DMRG_ERR_STATE.  Destroying a handle first releases the batch's
+ *     plans; the batch itself must still be destroyed (either order is safe).
  *   dmrg_batch_sigma: psi_dev[i], sigma_dev[i] (host arrays of n device
  *     pointers, psi_size doubles of problem i each).  use_graph = 1 captures the
  *     whole step into a CUDA graph on the first call (and whenever the buffer

@@ -165,6 +165,7 @@ class Dmrg:
         it = ctypes.c_int32()
         st = self.lib.dmrg_davidson(self.h, bond, ctypes.c_void_p(int(psi_ptr)), float(tol), int(max_iter),
                                     ctypes.byref(e), ctypes.byref(it))
+        self.last_status = st
         if check:
             self._check(st)
         return e.value, it.value

@@ -34,6 +34,7 @@ struct dmrg_batch {
   std::vector<double*> g_sig;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  bool dead = false;   // one of its handles was destroyed: plans released
 };
 
 namespace {
@@ -101,6 +102,26 @@ void free_graph(dmrg_batch* b) {
   b->g_sig.clear();
 }
 
+// release the merged plans (while the owner executor exists) and detach the
+// batch from its handles; afterwards the batch holds nothing but its own memory
+void retire(dmrg_batch* b) {
+  if (b->dead) return;
+  free_graph(b);
+  for (int id : {b->plan_hl, b->plan1, b->plan2})
+    if (id >= 0) b->owner->mix_plan_free(id);
+  b->plan_hl = b->plan1 = b->plan2 = -1;
+  b->owner->sync();
+  for (dmrg_handle* h : b->h) {
+    auto& v = h->batches;
+    for (size_t i = 0; i < v.size(); ++i)
+      if (v[i] == b) {
+        v.erase(v.begin() + long(i));
+        break;
+      }
+  }
+  b->dead = true;
+}
+
 // the batched step, issued on the shared stream (no allocation, no host wait)
 void issue(dmrg_batch* b, const double* const* psi, double* const* sig) {
   for (size_t i = 0; i < b->h.size(); ++i) b->h[i]->eng->batch_prologue(psi[i]);
@@ -149,6 +170,7 @@ dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int3
     b->plan1 = merge_plans(b->owner, p1);
     b->plan2 = merge_plans(b->owner, p2);
     b->owner->sync();
+    for (dmrg_handle* h : b->h) h->batches.push_back(b.get());
     *out = b.release();
     return DMRG_OK;
   });
@@ -158,6 +180,7 @@ dmrg_status dmrg_batch_sigma(dmrg_batch* b, const double* const* psi_dev, double
                              int32_t use_graph) {
   return guard([&]() -> dmrg_status {
     if (!b || !psi_dev || !sigma_dev) return fail(DMRG_ERR_ARG, "null argument");
+    if (b->dead) return fail(DMRG_ERR_STATE, "a handle of the batch was destroyed; destroy the batch");
     const size_t n = b->h.size();
     for (size_t i = 0; i < n; ++i) {
       if (!psi_dev[i] || !sigma_dev[i]) return fail(DMRG_ERR_ARG, "null buffer");
@@ -211,13 +234,23 @@ dmrg_status dmrg_batch_sigma(dmrg_batch* b, const double* const* psi_dev, double
 void dmrg_batch_destroy(dmrg_batch* b) {
   if (!b) return;
   try {
-    free_graph(b);
-    for (int id : {b->plan_hl, b->plan1, b->plan2})
-      if (id >= 0) b->owner->mix_plan_free(id);
-    b->owner->sync();
+    retire(b);
   } catch (...) {
   }
   delete b;
 }
 
 }  // extern "C"
+
+void dmrg_internal_handle_gone(dmrg_handle* h) {
+  // retire() edits h->batches: work on a copy
+  const std::vector<dmrg_batch*> live = h->batches;
+  for (dmrg_batch* b : live) {
+    try {
+      retire(b);
+    } catch (...) {
+      b->dead = true;
+    }
+  }
+  h->batches.clear();
+}

@@ -335,6 +335,7 @@ dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out) {
 void dmrg_destroy(dmrg_handle* h) {
   try {
     if (h) {
+      dmrg_internal_handle_gone(h);
       h->eng.reset();
       h->ex.reset();
       delete h;

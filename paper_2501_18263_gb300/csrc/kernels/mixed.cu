@@ -37,7 +37,7 @@ constexpr int BAR_BYTES = 256;
 constexpr int DRAIN_THREADS = 512;              // 16 warps: 4 lane quarters x 4 column quarters
 constexpr int DRAIN_COLS = 32;                  // accumulator columns per drain thread
 constexpr int NTHREADS = 32 + 32 + DRAIN_THREADS;
-constexpr int CHUNK = 4;                        // K stages per accumulator chunk (128 K)
+constexpr int CHUNK = 8;                        // K stages per accumulator chunk (256 K)
 constexpr long long WAIT_CYCLES = 3000000000LL; // about 1.5 s at 2 GHz (fits the 32-bit clock)
 constexpr uint32_t TMEM_COLS = 512;
 
@@ -488,7 +488,9 @@ __global__ void __maxnreg__(96)
           mbar_wait_warp(acc_full(b), (chunk >> 1) & 1, abort_flag, err, 3);
           fence_after();
           const uint32_t t0 = tq + 256u * b;
-          if (mine) {
+          // a tile of one chunk is its own running sum: sh = acc0 and sl = acc1
+          // exactly, already in place for the epilogue (nch is tile-uniform)
+          if (mine && nch > 1) {
 #pragma unroll
             for (int h = 0; h < DRAIN_COLS / 8; ++h) {
               float v0[8], v1[8];

@@ -112,9 +112,17 @@ def test_batch_rejects_a_re_prepared_handle_and_fp64_handles():
     torch.cuda.synchronize()
     batch = B.Batch([d], [3])
     batch.sigma([psi.data_ptr()], [out.data_ptr()])
-    d.prepare(2)
+    d.prepare(3)   # preparing again rebuilds the plans the batch was made of
     with pytest.raises(B.DmrgError) as e:
         batch.sigma([psi.data_ptr()], [out.data_ptr()])
+    assert e.value.status == B.ERR_STATE
+    batch.close()
+    # a handle destroyed before its batch: the batch answers ERR_STATE and still closes
+    batch = B.Batch([d], [3])
+    batch.sigma([psi.data_ptr()], [out.data_ptr()], graph=True)
+    d.close()
+    with pytest.raises(B.DmrgError) as e:
+        batch.sigma([psi.data_ptr()], [out.data_ptr()], graph=True)
     assert e.value.status == B.ERR_STATE
     batch.close()
     f = B.Dmrg(t, v, 4, 4, D=32, precision=B.PREC_FP64, stream=stream.cuda_stream)
@@ -124,4 +132,3 @@ def test_batch_rejects_a_re_prepared_handle_and_fp64_handles():
         B.Batch([f], [3])
     assert e.value.status == B.ERR_ARG
     f.close()
-    d.close()
