@@ -130,9 +130,9 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def measured_traffic(args, mixed):
-    """DRAM bytes per sigma of the tensor-core kernel from the committed ncu capture of
-    this workload, or None when the kernel source changed since it was taken."""
+def measured_capture(args, mixed):
+    """The committed ncu capture of this workload's tensor-core kernel (DRAM bytes and
+    tensor-pipe activity per launch), or None when the kernel source changed since."""
     path = os.path.join(ROOT, "profiles", "mixed_gemm_kernel_L32_D2048.json")
     try:
         rec = json.load(open(path))
@@ -142,7 +142,7 @@ def measured_traffic(args, mixed):
                 (w["L"], w["n_alpha"], w["n_beta"], w["D"], w["bond"]) !=
                 (args.L, args.na, args.nb, args.D, args.bond)):
             return None
-        return rec["traffic_bytes_per_sigma"]
+        return rec
     except (OSError, KeyError, ValueError):
         return None
 
@@ -273,6 +273,7 @@ def main():
     e2e_s = max_over_ranks((time.perf_counter() - t0) / ke, world, dev)
 
     pk, pk_kind = peaks()
+    cap = measured_capture(args, prec == B.PREC_MIXED_BF16)
     if prec == B.PREC_FP64:
         key = "gemm_f64"
         mhz = pk.get("sm_max_mhz", 2070.0)
@@ -319,7 +320,9 @@ def main():
         "roofline": {"bound": bound, "achieved": round(achieved, 4) if achieved else None,
                      "peak": round(peak, 3), "unit": unit,
                      "frac": round(achieved / peak, 4) if achieved else None,
-                     "traffic": measured_traffic(args, prec == B.PREC_MIXED_BF16),
+                     "traffic": cap["traffic_bytes_per_sigma"] if cap else None,
+                     "tensor_pipe_active_pct": ({x["plan"]: x.get("tensor_pipe_active_pct")
+                                                 for x in cap["launches_per_sigma"]} if cap else None),
                      "kernel": key, "peak_source": peak_kind,
                      "kernel_ms_per_step": round(kms, 3) if kms else None},
         "profile_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]},
@@ -473,6 +476,7 @@ def batched_bench(args, B, I):
     pp = [p.data_ptr() for p in psis]
     sp = [s.data_ptr() for s in sigs]
     batch = B.Batch(ds, bonds)
+    sched = batch.schedule()
 
     def timed(fn, k):
         for _ in range(3):
@@ -514,6 +518,7 @@ def batched_bench(args, B, I):
             "ms_per_step": {"one_by_one": round(t_seq * 1e3, 3), "batched": round(t_eager * 1e3, 3),
                             "batched_graph": round(t_graph * 1e3, 3)},
             "abs_dE_mixed_vs_fp64": {"max": max(de), "median": float(np.median(de))},
+            "schedule": sched,
             "L_D": [[m[0], m[3]] for m in meta]}
 
 

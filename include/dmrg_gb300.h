@@ -220,6 +220,14 @@ typedef struct dmrg_batch dmrg_batch;
 dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int32_t* bonds, dmrg_batch** out);
 dmrg_status dmrg_batch_sigma(dmrg_batch* b, const double* const* psi_dev, double* const* sigma_dev,
                              int32_t use_graph);
+/* Tile schedule of the batch's merged launches, chosen at dmrg_batch_create by
+ * timing every candidate on the GPU (skipped, order 0, while kernel timing is on):
+ * order3[k] for k = 0 local term, 1 stage 1, 2 stage 2, with 0 = longest tile
+ * first over all problems, 1 = problems in batch order with each problem's tiles
+ * together, 2 = problems by decreasing work with each problem's tiles together;
+ * ms9[3k + o] (host, may be NULL) = measured milliseconds of order o for stage k
+ * (0 where not timed).  The order changes only the time, never the result. */
+dmrg_status dmrg_batch_schedule(dmrg_batch* b, int32_t* order3, float* ms9);
 void dmrg_batch_destroy(dmrg_batch* b);
 
 void dmrg_destroy(dmrg_handle* h);

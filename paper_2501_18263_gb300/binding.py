@@ -19,7 +19,7 @@ PREC_FP64, PREC_MIXED_BF16 = 0, 1
 
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
            "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_stats",
-           "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_destroy", "dmrg_destroy",
+           "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
            "dmrg_last_error"]
 SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
 PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "jacobi", "gemm_bf16x", "split", "gemm_bf16x_stage1"]
@@ -67,6 +67,7 @@ def load_library(path: str | None = None):
         "dmrg_profile": ([vp, i32, dp], ctypes.c_int),
         "dmrg_batch_create": ([i32, ctypes.POINTER(vp), ip, ctypes.POINTER(vp)], ctypes.c_int),
         "dmrg_batch_sigma": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32], ctypes.c_int),
+        "dmrg_batch_schedule": ([vp, ip, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "dmrg_batch_destroy": ([vp], None),
         "dmrg_destroy": ([vp], None),
         "dmrg_last_error": ([], ctypes.c_char_p),
@@ -231,6 +232,13 @@ class Batch:
         ps = (ctypes.c_void_p * n)(*[int(x) for x in psi_ptrs])
         ss = (ctypes.c_void_p * n)(*[int(x) for x in sig_ptrs])
         self._check(self.lib.dmrg_batch_sigma(self.b, ps, ss, 1 if graph else 0))
+
+    def schedule(self):
+        """Tile order chosen per stage (local term, stage 1, stage 2) and the ms of each candidate."""
+        o = (ctypes.c_int32 * 3)()
+        ms = (ctypes.c_float * 9)()
+        self._check(self.lib.dmrg_batch_schedule(self.b, o, ms))
+        return {"order": list(o), "ms": [list(ms[3 * k:3 * k + 3]) for k in range(3)]}
 
     def close(self):
         if getattr(self, "b", None):

@@ -35,6 +35,8 @@ struct dmrg_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool dead = false;   // one of its handles was destroyed: plans released
+  int order[3] = {0, 0, 0};                  // chosen tile order: local term, stage 1, stage 2
+  float ms[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // measured ms per candidate order
 };
 
 namespace {
@@ -64,12 +66,22 @@ dmrg_status guard(F&& f) {
   }
 }
 
-// one plan in the owner's executor made of the given plans of several executors
-int merge_plans(dmrg::Exec* owner, const std::vector<std::pair<dmrg::Exec*, int>>& parts) {
+// one plan made of the given plans of several executors: problems, segments and
+// gathered-row tables concatenated, indices offset
+struct Merged {
   std::vector<dmrg::MixProb> P;
   std::vector<dmrg::MixSeg> S;
   std::vector<int64_t> bcol, ccol;
   std::vector<float> acol;
+};
+
+Merged merge(const std::vector<std::pair<dmrg::Exec*, int>>& parts) {
+  Merged m;
+  auto& P = m.P;
+  auto& S = m.S;
+  auto& bcol = m.bcol;
+  auto& ccol = m.ccol;
+  auto& acol = m.acol;
   for (const auto& pr : parts) {
     if (pr.second < 0) continue;
     const dmrg::Exec::MixPlanHost& H = pr.first->mix_plan_host(pr.second);
@@ -89,8 +101,36 @@ int merge_plans(dmrg::Exec* owner, const std::vector<std::pair<dmrg::Exec*, int>
     ccol.insert(ccol.end(), H.ccol.begin(), H.ccol.end());
     acol.insert(acol.end(), H.acol.begin(), H.acol.end());
   }
-  if (P.empty()) return -1;
-  return owner->mix_plan_g(P, S, bcol, ccol, acol);
+  return m;
+}
+
+// Autotuner of the merged launch's tile schedule: every candidate order is built
+// and timed on the GPU (CUDA events, one warm-up run), the fastest is kept.  All
+// orders compute every output tile identically, so the choice changes only the
+// time.  Running a plan here is harmless: it writes only the handles' own
+// intermediate buffers, which every sigma step rewrites before reading.
+int build_tuned(dmrg::Exec* owner, const Merged& m, bool tune, int* order_out, float* ms_out) {
+  if (m.P.empty()) return -1;
+  if (!tune) {
+    *order_out = 0;
+    return owner->mix_plan_ordered(m.P, m.S, m.bcol, m.ccol, m.acol, 0);
+  }
+  int best = -1;
+  float best_ms = 0.f;
+  for (int order = 0; order < 3; ++order) {
+    const int id = owner->mix_plan_ordered(m.P, m.S, m.bcol, m.ccol, m.acol, order);
+    const float ms = owner->mix_time(id, 2);
+    ms_out[order] = ms;
+    if (best < 0 || ms < best_ms) {
+      if (best >= 0) owner->mix_plan_free(best);
+      best = id;
+      best_ms = ms;
+      *order_out = order;
+    } else {
+      owner->mix_plan_free(id);
+    }
+  }
+  return best;
 }
 
 void free_graph(dmrg_batch* b) {
@@ -166,9 +206,10 @@ dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int3
       p1.push_back({h->eng->exec(), h->eng->mix_plan1()});
       p2.push_back({h->eng->exec(), h->eng->mix_plan2()});
     }
-    b->plan_hl = merge_plans(b->owner, hl);
-    b->plan1 = merge_plans(b->owner, p1);
-    b->plan2 = merge_plans(b->owner, p2);
+    const bool tune = !b->owner->profiling();   // timing runs would pollute the caller's kernel profile
+    b->plan_hl = build_tuned(b->owner, merge(hl), false, &b->order[0], b->ms[0]);
+    b->plan1 = build_tuned(b->owner, merge(p1), tune, &b->order[1], b->ms[1]);
+    b->plan2 = build_tuned(b->owner, merge(p2), tune, &b->order[2], b->ms[2]);
     b->owner->sync();
     for (dmrg_handle* h : b->h) h->batches.push_back(b.get());
     *out = b.release();
@@ -227,6 +268,18 @@ dmrg_status dmrg_batch_sigma(dmrg_batch* b, const double* const* psi_dev, double
     }
     b->owner->sync();
     if (b->owner->device_error()) return fail(DMRG_ERR_TIMEOUT, "a tensor-core pipeline wait gave up; destroy the handles");
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_batch_schedule(dmrg_batch* b, int32_t* order3, float* ms9) {
+  return guard([&]() -> dmrg_status {
+    if (!b || !order3) return fail(DMRG_ERR_ARG, "null argument");
+    for (int k = 0; k < 3; ++k) {
+      order3[k] = b->order[k];
+      if (ms9)
+        for (int o = 0; o < 3; ++o) ms9[3 * k + o] = b->ms[k][o];
+    }
     return DMRG_OK;
   });
 }

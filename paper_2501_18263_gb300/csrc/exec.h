@@ -160,7 +160,15 @@ class Exec {
   virtual int mix_plan_g(const std::vector<MixProb>& p, const std::vector<MixSeg>& s,
                          const std::vector<int64_t>& bcol, const std::vector<int64_t>& ccol,
                          const std::vector<float>& acol) = 0;
+  // the same with a tile schedule: order 0 = longest tile first over the whole
+  // list (the default), 1 = problems in the given order, each problem's tiles
+  // together, 2 = problems by decreasing total work, each problem's tiles together
+  virtual int mix_plan_ordered(const std::vector<MixProb>& p, const std::vector<MixSeg>& s,
+                               const std::vector<int64_t>& bcol, const std::vector<int64_t>& ccol,
+                               const std::vector<float>& acol, int order) = 0;
   virtual void mix_run(int plan) = 0;
+  // milliseconds per run of a plan (CUDA events on the stream, after one warm-up run)
+  virtual float mix_time(int plan, int reps) = 0;
   virtual void mix_plan_free(int plan) = 0;
   // host copy of a plan's problems, segments and gathered-row tables (kept so that
   // plans of several problems can be merged into one grouped launch)

@@ -825,6 +825,11 @@ class CudaExec : public Exec {
   }
   int mix_plan_g(const std::vector<MixProb>& p, const std::vector<MixSeg>& s, const std::vector<int64_t>& bcol,
                  const std::vector<int64_t>& ccol, const std::vector<float>& acol) override {
+    return mix_plan_ordered(p, s, bcol, ccol, acol, 0);
+  }
+  int mix_plan_ordered(const std::vector<MixProb>& p, const std::vector<MixSeg>& s, const std::vector<int64_t>& bcol,
+                       const std::vector<int64_t>& ccol, const std::vector<float>& acol, int order) override {
+    if (order < 0 || order > 2) throw std::runtime_error("mix_plan: unknown tile order");
     for (const MixSeg& g : s) {
       // blocked split matrices are built of 128-byte core-matrix pairs: every
       // bulk copy source is 16-byte aligned when the matrix base is
@@ -857,10 +862,21 @@ class CudaExec : public Exec {
         }
     }
     {
-      // persistent CTAs take tiles in strides: longest first balances the load
+      // persistent CTAs take tiles in strides: longest first balances the load;
+      // orders 1 and 2 keep each problem's tiles together (operand slabs shared
+      // by the tiles of one output block are then read at about the same time)
       std::vector<size_t> ord(tiles.size());
       for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
-      std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+      if (order == 0) {
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+      } else if (order == 2) {
+        std::vector<int64_t> pw(p.size(), 0);
+        for (size_t i = 0; i < tiles.size(); ++i) pw[tiles[i].prob] += work[i];
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+          const int pa = tiles[a].prob, pb = tiles[b].prob;
+          return pa != pb && (pw[pa] != pw[pb] ? pw[pa] > pw[pb] : pa < pb);
+        });
+      }
       std::vector<MixTile> t2;
       t2.reserve(tiles.size());
       for (size_t i : ord) t2.push_back(tiles[i]);
@@ -892,6 +908,19 @@ class CudaExec : public Exec {
   }
   void mix_plan_free(int id) override { mix_free(id); }
   const MixPlanHost& mix_plan_host(int id) const override { return mplans_.at(id).host; }
+  float mix_time(int id, int reps) override {
+    mix_run(id);
+    cudaEvent_t a = ev(), b = ev();
+    CK(cudaEventRecord(a, st_));
+    for (int r = 0; r < reps; ++r) mix_run(id);
+    CK(cudaEventRecord(b, st_));
+    CK(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    pool_.push_back(a);
+    pool_.push_back(b);
+    return ms / float(std::max(1, reps));
+  }
   void* stream() const override { return st_; }
   bool profiling() const override { return prof_; }
   void split_plan_free(int id) override {

@@ -47,6 +47,9 @@ def test_batched_sigma_is_bit_identical_to_single_problem_sigma():
     stream = torch.cuda.Stream()
     ds, bonds, psis, refs = _setup(stream)
     batch = B.Batch(ds, bonds)
+    sch = batch.schedule()          # tile orders picked by timing every candidate
+    assert all(0 <= o <= 2 for o in sch["order"])
+    assert min(sch["ms"][1]) > 0 and min(sch["ms"][2]) > 0
     outs = [torch.full_like(p, float("nan")) for p in psis]
     batch.sigma([p.data_ptr() for p in psis], [o.data_ptr() for o in outs], graph=False)
     for o, r in zip(outs, refs):
