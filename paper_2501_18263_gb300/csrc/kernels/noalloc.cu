@@ -64,6 +64,8 @@ extern "C" dmrg_status dmrg_sigma_host_noalloc(dmrg_handle* h, int32_t bond, con
     ex->h2d(base, psi_host, size_t(n) * sizeof(double));
     h->eng->sigma_precision(base, base + kMaxPsi, h->eng->problem().precision);
     ex->d2h(sigma_host, base + kMaxPsi, size_t(n) * sizeof(double));
+    // a bounded wait inside the tensor-core kernel that gave up leaves a nonzero word
+    if (ex->device_error()) return fail(DMRG_ERR_TIMEOUT, "a tensor-core pipeline wait gave up; destroy the handle");
     return DMRG_OK;
   } catch (const dmrg::CudaError& e) {
     return fail(DMRG_ERR_CUDA, e.what());
