@@ -324,6 +324,11 @@ def main():
                      "tensor_pipe_active_pct": ({x["plan"]: x.get("tensor_pipe_active_pct")
                                                  for x in cap["launches_per_sigma"]} if cap else None),
                      "kernel": key, "peak_source": peak_kind,
+                     # the split-BF16 path performs six BF16 products per algorithmic multiply-add,
+                     # so its own ceiling in algorithmic flops is the BF16 peak / 6
+                     "split_ceiling": round(peak / 6, 3) if key != "gemm_f64" else None,
+                     "frac_of_split_ceiling": (round(achieved / (peak / 6), 4)
+                                               if (achieved and key != "gemm_f64") else None),
                      "kernel_ms_per_step": round(kms, 3) if kms else None},
         "profile_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]},
         "fp64": fp64,

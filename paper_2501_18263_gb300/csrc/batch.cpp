@@ -207,10 +207,16 @@ dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int3
       p2.push_back({h->eng->exec(), h->eng->mix_plan2()});
     }
     const bool tune = !b->owner->profiling();   // timing runs would pollute the caller's kernel profile
-    b->plan_hl = build_tuned(b->owner, merge(hl), false, &b->order[0], b->ms[0]);
-    b->plan1 = build_tuned(b->owner, merge(p1), tune, &b->order[1], b->ms[1]);
-    b->plan2 = build_tuned(b->owner, merge(p2), tune, &b->order[2], b->ms[2]);
-    b->owner->sync();
+    try {
+      b->plan_hl = build_tuned(b->owner, merge(hl), false, &b->order[0], b->ms[0]);
+      b->plan1 = build_tuned(b->owner, merge(p1), tune, &b->order[1], b->ms[1]);
+      b->plan2 = build_tuned(b->owner, merge(p2), tune, &b->order[2], b->ms[2]);
+      b->owner->sync();
+    } catch (...) {
+      for (int id : {b->plan_hl, b->plan1, b->plan2})
+        if (id >= 0) b->owner->mix_plan_free(id);
+      throw;
+    }
     for (dmrg_handle* h : b->h) h->batches.push_back(b.get());
     *out = b.release();
     return DMRG_OK;
