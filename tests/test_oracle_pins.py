@@ -38,7 +38,7 @@ def test_spinless_torus_printed_energies():
     assert w[0] < w[1]
 
 
-@pytest.mark.parametrize("L", [2, 3])
+@pytest.mark.parametrize("L", [2, 3, 4])
 def test_fci_sigma_equals_jordan_wigner_fock_matrix(L):
     """fci.c (bit-string signs) against an independent Kronecker-product JW construction, every sector."""
     t, v = I.synthetic_integrals(L, 7 + L)
