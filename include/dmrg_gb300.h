@@ -172,9 +172,10 @@ dmrg_status dmrg_sweep_phases(dmrg_handle* h, double* seconds5);
  *   g2[((i*L+j)*L+k)*L+l] += <x| sum_st a+_is a+_kt a_lt a_js |y>
  * so that dE/dt = g1 and dE/dv = g2/2 for x = y = the normalised eigenvector.
  * g1, g2 are device buffers (L^2 and L^4 doubles).
- * NOT BUILT in this version: the call checks its arguments and the bond
- * index, then returns DMRG_ERR_ARG with the message "dmrg_sigma_backward: not
- * available in this build"; it prepares nothing and writes nothing. */
+ * NOT IMPLEMENTED in this version of the library: the call checks its
+ * arguments and the bond index, then returns DMRG_ERR_ARG with the message
+ * "dmrg_sigma_backward: not implemented in this version of the library"; it
+ * prepares nothing and writes nothing. */
 dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi_dev, const double* lam_dev,
                                 double* g1_dev, double* g2_dev);
 

@@ -919,7 +919,7 @@ void Engine::batch_epilogue(double* sig) {
 
 void Engine::rdm(const double* lam, const double* psi, double* g1, double* g2) {
   (void)lam; (void)psi; (void)g1; (void)g2;
-  throw std::runtime_error("dmrg_sigma_backward: not available in this build");
+  throw std::runtime_error("dmrg_sigma_backward: not implemented in this version of the library");
 }
 
 void Engine::diagonal(double* d) {
