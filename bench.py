@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--batched", type=int, default=0,
                     help="also time the batched form on this many independent problems (L ~ U[10,20], "
                          "electrons = L with alpha/beta split within +-2, D in {256,512,1024}, seeds 100..)")
+    ap.add_argument("--sweep-ramp", default="",
+                    help="comma list of bond dimensions: one full sweep at each, in order, on one handle from the "
+                         "seeded product-state basis (the D ramp of the headline sweep); per-sweep times and energies")
     ap.add_argument("--compare-davidson", default="",
                     help="L,na,nb,D: Davidson (Diag_H) at the centre bond of a fixed seeded basis in FP64 and in "
                          "split-BF16 with FP64 refinement, same start vector; times, energies and |dE|")
@@ -369,6 +372,8 @@ def main():
     extras = []
     if args.batched > 0:
         extras.append(("batched", lambda: batched_bench(args, B, I)))
+    if args.sweep_ramp:
+        extras.append(("sweep_ramp", lambda: sweep_ramp(args, B, t, v, prec, stream)))
     if args.compare_davidson:
         extras.append(("davidson_compare", lambda: compare_davidson(args, B, I, stream)))
     if args.compare_sweeps:
@@ -382,6 +387,25 @@ def main():
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def sweep_ramp(args, B, t, v, prec, stream):
+    """One full sweep per bond dimension of the ramp, continuing on one handle: wall seconds,
+    Sec. 4.1 phase split and energy of each sweep."""
+    import torch
+    Ds = [int(x) for x in args.sweep_ramp.split(",")]
+    d = B.Dmrg(t, v, args.na, args.nb, D=Ds[0], precision=prec, seed=args.seed, stream=stream.cuda_stream)
+    res = {"workload": f"one full sweep L->R->L per D in {Ds} on one handle, L={args.L}, {args.na}a+{args.nb}b, "
+                       f"from the seeded product-state basis, Davidson tol {args.sweep_tol:g}", "sweeps": []}
+    for D in Ds:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e = d.sweep(1, [D], tol=args.sweep_tol)
+        torch.cuda.synchronize()
+        res["sweeps"].append({"D": D, "seconds": round(time.perf_counter() - t0, 2), "energy": float(e[0]),
+                              "phases_s": {k: round(x, 2) for k, x in d.sweep_phases().items()}})
+    d.close()
+    return res
 
 
 def compare_davidson(args, B, I, stream):
