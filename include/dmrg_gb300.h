@@ -189,7 +189,8 @@ dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out16);
 /* Kernel timing with CUDA events on the handle's stream (this library's
  * kernels only).  mode = 1: reset counters and start; mode = 0: stop and write
  * out14[2c] = milliseconds and out14[2c+1] = launches for the kernel classes
- * c = 0 FP64 GEMM, 1 blocking (kron), 2 vector, 3 Jacobi eigen, 4 split-BF16
+ * c = 0 FP64 GEMM, 1 blocking (kron), 2 vector, 3 eigensolvers (Rayleigh-Ritz
+ * Jacobi and the density-matrix Householder + QL), 4 split-BF16
  * tensor-core GEMM of sigma stage 2 (and accumulating products), 5 split /
  * pack / reduce, 6 split-BF16 tensor-core GEMM of sigma stage 1.
  * out14 may be NULL when mode = 1. */
@@ -221,7 +222,8 @@ typedef struct dmrg_batch dmrg_batch;
 dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int32_t* bonds, dmrg_batch** out);
 dmrg_status dmrg_batch_sigma(dmrg_batch* b, const double* const* psi_dev, double* const* sigma_dev,
                              int32_t use_graph);
-/* Tile schedule of the batch's merged launches, chosen at dmrg_batch_create by
+/* Tile schedule of the batch's merged launches (an implementation parameter;
+ * the paper has no counterpart), chosen at dmrg_batch_create by
  * timing every candidate on the GPU (skipped, order 0, while kernel timing is on):
  * order3[k] for k = 0 local term, 1 stage 1, 2 stage 2, with 0 = longest tile
  * first over all problems, 1 = problems in batch order with each problem's tiles

@@ -22,7 +22,7 @@ SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "d
            "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
            "dmrg_last_error"]
 SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
-PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "jacobi", "gemm_bf16x", "split", "gemm_bf16x_stage1"]
+PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "eigen", "gemm_bf16x", "split", "gemm_bf16x_stage1"]
 
 
 class DmrgError(RuntimeError):

@@ -2,8 +2,9 @@
 //   gemm_f64      grouped, segmented FP64 GEMM (the FP64 sigma / Ren / StVec path)
 //   kron          grouped Kronecker accumulation (operator blocking)
 //   mdot/lincomb  Davidson Gram-Schmidt and Ritz vectors (deterministic reductions)
-//   ritz/syev     cyclic Jacobi eigen-solvers for the Rayleigh-Ritz matrix and the
-//                 density matrices of the truncation
+//   ritz          cyclic Jacobi eigensolver of the small Rayleigh-Ritz matrix
+//   syev          Householder tridiagonalisation + implicit QL eigensolver of the
+//                 density matrices of the truncation (one CTA per sector block)
 // All work is ordered on one stream; allocations are stream-ordered.
 #include <cuda_runtime.h>
 
