@@ -15,6 +15,9 @@ Contents
     as explicit Fock-space vectors (exact for L <= 12).
   * layout: the oracle's own reading of the block-sparse psi layout (integer
     tables compared bit-exactly with the CUDA path's).
+  * expm_skew / rotate_integrals / orbital_gradient: orbital rotations
+    U = exp(kappa) of the integrals (Sec. 2.2) and the generalised-Fock gradient
+    dE/dkappa from the one- and two-particle density matrices.
 """
 from __future__ import annotations
 
@@ -338,3 +341,53 @@ def projected_sigma(t, v, na, nb, bp, psi_blocks, return_parts=False):
     if return_parts:
         return out, dict(U=U, V=V, leak=leak, x=x, y=y)
     return out
+
+
+# ----------------------------------------------------------------------------
+# Orbital rotations and the orbital gradient (Sec. 2.2: c~+ = U c+ keeps the
+# form of H with rotated integrals; the gradient of E with respect to the
+# generator kappa of U = exp(kappa) is what mode optimisation follows)
+# ----------------------------------------------------------------------------
+
+def expm_skew(kappa, terms=18):
+    """exp(kappa) for a real antisymmetric kappa by scaling and squaring of the Taylor series.
+
+    kappa / 2^s has norm <= 1/2, its exponential is summed to `terms` terms (error
+    below 2^-60 relative), then squared s times.  The result is orthogonal with
+    determinant 1.
+    """
+    k = np.asarray(kappa, dtype=np.float64)
+    nrm = float(np.linalg.norm(k, 1)) if k.size else 0.0
+    s = max(0, int(np.ceil(np.log2(nrm / 0.5)))) if nrm > 0.5 else 0
+    a = k / (2.0 ** s)
+    out = np.eye(k.shape[0])
+    term = np.eye(k.shape[0])
+    for n in range(1, terms + 1):
+        term = term @ a / n
+        out = out + term
+    for _ in range(s):
+        out = out @ out
+    return out
+
+
+def rotate_integrals(t, v, U):
+    """Integrals of the rotated orbitals: t' = U t U^T, v'_abcd = sum U_ai U_bj U_ck U_dl v_ijkl."""
+    return U @ t @ U.T, np.einsum("ai,bj,ck,dl,ijkl->abcd", U, U, U, U, v, optimize=True)
+
+
+def orbital_gradient(t, v, na, nb, x):
+    """dE/dkappa_pq (p > q) of E(kappa) = <x| H(exp(kappa)) |x> at kappa = 0 for fixed
+    determinant coefficients x, with kappa_qp = -kappa_pq; returned as the antisymmetric
+    matrix G with G[p, q] = dE/dkappa_pq.
+
+    To first order t' = t + kappa t + t kappa^T and each index of v picks up kappa the
+    same way, so with g1, g2 the one- and two-particle density matrices of x (fci_rdm12)
+    and the generalised Fock matrix
+        F_pq = sum_r t_pr g1_qr + sum_rst v_prst g2_qrst,
+    the derivative with respect to an unconstrained kappa_pq is 2 F_qp, and the
+    antisymmetric constraint gives G_pq = 2 (F_qp - F_pq).
+    """
+    L = t.shape[0]
+    g1, g2 = fci_rdm12(na, nb, x, x, L)
+    F = np.einsum("pr,qr->pq", t, g1) + np.einsum("prst,qrst->pq", v, g2, optimize=True)
+    return 2.0 * (F.T - F)

@@ -208,3 +208,51 @@ def test_psi_layout_is_sector_conserving():
     assert np.all(np.diff(lay[:, 6]) == (lay[:-1, 4] * lay[:-1, 5]))
     assert [tuple(r[:2]) for r in lay] == sorted(tuple(r[:2]) for r in lay)
     assert [blk.shape for (_, _, blk) in bp.psi] == [tuple(r[4:6]) for r in lay]
+
+
+def test_expm_skew_closed_forms():
+    """exp of a plane-rotation generator is the rotation matrix; orthogonal, det 1, and equal
+    to an independent eigendecomposition route for a random generator."""
+    for th in (0.3, 2.0, 7.5):
+        k = np.array([[0.0, th], [-th, 0.0]])
+        np.testing.assert_allclose(O.expm_skew(k), [[np.cos(th), np.sin(th)], [-np.sin(th), np.cos(th)]],
+                                   atol=1e-14)
+    rng = np.random.default_rng(4)
+    a = rng.standard_normal((6, 6))
+    k = 1.7 * (a - a.T)
+    U = O.expm_skew(k)
+    np.testing.assert_allclose(U @ U.T, np.eye(6), atol=1e-13)
+    assert np.linalg.det(U) == pytest.approx(1.0, abs=1e-12)
+    # i*kappa is Hermitian: exp(kappa) = V exp(-i w) V^H from its eigendecomposition
+    w, V = np.linalg.eigh(1j * k)
+    ref = (V * np.exp(-1j * w)) @ V.conj().T
+    np.testing.assert_allclose(U, ref.real, atol=1e-12)
+    assert np.abs(ref.imag).max() < 1e-12
+
+
+def test_orbital_gradient_matches_finite_differences_and_vanishes_at_fci():
+    """The generalised-Fock orbital gradient against central differences of E(kappa) evaluated
+    through fci.c with rotated integrals (fixed coefficients), and the Brillouin condition: it
+    vanishes at the FCI ground state, whose energy is stationary under orbital rotations."""
+    L, na, nb = 5, 3, 2
+    t, v = I.synthetic_integrals(L, 21)
+    rng = np.random.default_rng(22)
+    x = rng.standard_normal(O.fci_dim(L, na, nb))
+    x /= np.linalg.norm(x)
+    G = O.orbital_gradient(t, v, na, nb, x)
+    np.testing.assert_allclose(G, -G.T, atol=1e-12)
+
+    def energy(kappa):
+        tr, vr = O.rotate_integrals(t, v, O.expm_skew(kappa))
+        return float(x @ O.fci_sigma(tr, vr, na, nb, x))
+
+    h = 1e-5
+    for (p, q) in ((1, 0), (3, 1), (4, 2), (4, 0)):
+        k = np.zeros((L, L))
+        k[p, q], k[q, p] = h, -h
+        fd = (energy(k) - energy(-k)) / (2 * h)
+        assert fd == pytest.approx(G[p, q], abs=1e-7 * max(1.0, abs(G[p, q])))
+    assert np.abs(G).max() > 1e-2                       # a random state is far from stationary
+    w, U = O.fci_lowest(t, v, na, nb)
+    G0 = O.orbital_gradient(t, v, na, nb, U[:, 0])
+    assert np.abs(G0).max() < 1e-9
