@@ -66,3 +66,19 @@ def test_batch_argument_errors_without_a_device(lib):
     assert b"null handle" in L.dmrg_last_error()
     assert L.dmrg_batch_sigma(None, None, None, 0) == binding.ERR_ARG
     L.dmrg_batch_destroy(None)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/dmrg_gb300.h compiles as C99 and every declared entry point links against the library."""
+    names = _declared()
+    src = tmp_path / "use.c"
+    body = "\n".join(f"  p[{i}] = (void (*)(void)){n};" for i, n in enumerate(names))
+    src.write_text('#include "dmrg_gb300.h"\n#include <stddef.h>\n'
+                   f"int main(void) {{\n  void (*p[{len(names)}])(void);\n{body}\n"
+                   "  return p[0] == NULL;\n}\n")
+    from paper_2501_18263_gb300 import build
+    lib = build.build()
+    exe = tmp_path / "use"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe), lib, "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
