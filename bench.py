@@ -461,17 +461,6 @@ def compare_sweeps(args, B, I, stream):
     return res
 
 
-def batched_problem(i):
-    """Problem i of the batched workload (seed 100 + i)."""
-    seed = 100 + i
-    rng = np.random.default_rng(seed)
-    L = int(rng.integers(10, 21))
-    splits = [s for s in range(-2, 3) if (s - L) % 2 == 0]
-    s = int(rng.choice(splits))
-    D = int(rng.choice([256, 512, 1024]))
-    return L, (L + s) // 2, (L - s) // 2, D, seed
-
-
 def batched_bench(args, B, I):
     """Split-BF16 sigma steps of many independent problems (each at its centre bond):
     one by one through dmrg_sigma, batched in shared grouped launches, and batched
@@ -480,7 +469,7 @@ def batched_bench(args, B, I):
     stream = torch.cuda.Stream()
     ds, bonds, psis, sigs, flops, meta = [], [], [], [], 0, []
     for i in range(args.batched):
-        L, na, nb, D, seed = batched_problem(i)
+        L, na, nb, D, seed = I.batched_problem(i)
         bond = L // 2 - 1
         t, v = I.synthetic_integrals(L, seed)
         bp = I.bond_problem(L, na, nb, D, bond, seed=seed + 1000)

@@ -291,9 +291,14 @@ def random_psi_like(bp: BondProblem, seed):
     return [(a, b, rng.standard_normal(blk.shape)) for (a, b, blk) in bp.psi]
 
 
-def electron_split(L, seed):
-    """Batched-workload electron counts: N = L, n_alpha - n_beta uniform over allowed values in [-2, 2]."""
+def batched_problem(i):
+    """Problem i of the batched workload: seed 100 + i; from one generator with that seed,
+    L ~ U{10..20}, n_alpha - n_beta uniform over the values in [-2, 2] of L's parity
+    (N = L electrons), D uniform in {256, 512, 1024}.  Returns (L, na, nb, D, seed)."""
+    seed = 100 + i
     rng = np.random.default_rng(seed)
-    allowed = [s for s in range(-2, 3) if (L + s) % 2 == 0]
-    s = int(rng.choice(allowed))
-    return (L + s) // 2, (L - s) // 2
+    L = int(rng.integers(10, 21))
+    splits = [s for s in range(-2, 3) if (s - L) % 2 == 0]
+    s = int(rng.choice(splits))
+    D = int(rng.choice([256, 512, 1024]))
+    return L, (L + s) // 2, (L - s) // 2, D, seed

@@ -5,15 +5,10 @@ stated properties are checked here: the symmetries and positive semidefiniteness
 of the synthetic integrals, orthonormal isometries, particle-number-conserving
 sector tables, a normalised psi, and the batched workload's ranges.
 """
-import os
-import sys
-
 import numpy as np
 import pytest
 
 from paper_2501_18263_gb300 import inputs as I
-
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.mark.parametrize("L,seed", [(4, 1), (8, 3), (12, 9)])
@@ -64,10 +59,10 @@ def test_bond_problem_bases_are_isometries_and_conserve_particles(kind, L, na, n
 
 
 def test_batched_workload_recipe():
-    sys.path.insert(0, ROOT)
-    import bench
-    probs = [bench.batched_problem(i) for i in range(64)]
-    assert probs == [bench.batched_problem(i) for i in range(64)]   # seeded
+    probs = [I.batched_problem(i) for i in range(64)]
+    assert probs == [I.batched_problem(i) for i in range(64)]   # seeded
+    # the draws behind the measured batched runs (first problems: L, D)
+    assert [(p[0], p[3]) for p in probs[:4]] == [(18, 256), (13, 1024), (14, 512), (16, 256)]
     for L, na, nb, D, seed in probs:
         assert 10 <= L <= 20 and na + nb == L and abs(na - nb) <= 2
         assert D in (256, 512, 1024)
