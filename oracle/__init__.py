@@ -15,6 +15,9 @@ Contents
     as explicit Fock-space vectors (exact for L <= 12).
   * layout: the oracle's own reading of the block-sparse psi layout (integer
     tables compared bit-exactly with the CUDA path's).
+  * truncation_keep / dmrg_two_site: the density-matrix truncation rule and a
+    plain two-site DMRG sweep (dense within sectors, explicit basis vectors,
+    small L) for sweep-level energies.
   * expm_skew / rotate_integrals / orbital_gradient: orbital rotations
     U = exp(kappa) of the integrals (Sec. 2.2) and the generalised-Fock gradient
     dE/dkappa from the one- and two-particle density matrices.
@@ -391,3 +394,146 @@ def orbital_gradient(t, v, na, nb, x):
     g1, g2 = fci_rdm12(na, nb, x, x, L)
     F = np.einsum("pr,qr->pq", t, g1) + np.einsum("prst,qrst->pq", v, g2, optimize=True)
     return 2.0 * (F.T - F)
+
+
+# ----------------------------------------------------------------------------
+# Plain two-site DMRG (Sec. 2.1: the ALS sweep over site pairs, Eq. DefinitionMPS;
+# Sec. 2.3: U(1) x U(1) sectors), dense within sectors, every basis written out as
+# explicit vectors over the configurations of its sites.  Small L only.
+# ----------------------------------------------------------------------------
+
+def truncation_keep(weights, D, rel_gap=1e-10):
+    """Indices of the kept states for the density-matrix weights `weights` (one array per
+    sector, in sector order): sort descending with ties broken by (sector, index), keep the
+    largest n <= D such that the n-th and (n+1)-th weights differ by more than
+    rel_gap * w_max (a near-degenerate group is kept or dropped whole); if no such n >= 1
+    exists, a group larger than D has to be split and n = D.  Returns [(sector, index)]."""
+    allw = [(-float(w), k, i) for k, ws in enumerate(weights) for i, w in enumerate(ws)]
+    allw.sort()
+    m = len(allw)
+    if m <= D:
+        return [(k, i) for (_, k, i) in allw]
+    wmax = -allw[0][0]
+    n = D
+    while n >= 1 and (-allw[n - 1][0]) - (-allw[n][0]) <= rel_gap * wmax:
+        n -= 1
+    if n < 1:
+        n = D
+    return [(k, i) for (_, k, i) in allw[:n]]
+
+
+def _site_q(s):
+    return LOCAL_Q[s]
+
+
+def _block_configs_q(nsites):
+    """(n_alpha, n_beta) of every configuration of nsites sites (site 0 most significant)."""
+    q = np.zeros((4 ** nsites, 2), dtype=np.int64)
+    for c in range(4 ** nsites):
+        x = c
+        for _ in range(nsites):
+            s = x % 4
+            x //= 4
+            q[c] += LOCAL_Q[s]
+    return q
+
+
+def dmrg_two_site(t, v, na, nb, D, n_sweeps):
+    """Energies of n_sweeps two-site sweeps (left to right over bonds 0..L-3, then right to
+    left over L-2..1; the energy of a sweep is the eigenvalue at its last step).
+
+    The initial right blocks are complete (every configuration of their sites), so the first
+    steps solve the problem exactly within the left basis kept so far.  At each bond the
+    effective Hamiltonian P^T H P (P embeds left basis x site x site x right basis into the
+    determinant space; H applied by fci_sigma) is built column by column and diagonalised
+    densely; the density matrix of the enlarged block is diagonalised per sector and the
+    states are kept by truncation_keep.
+    """
+    L = t.shape[0]
+    cfg = config_index(L, na, nb)
+    N = np.array([na, nb])
+
+    def full_basis(nsites):
+        V = np.eye(4 ** nsites)
+        return V, _block_configs_q(nsites)
+
+    # blocks: left[k] = basis of sites 0..k-1 (k = 0..L-2), right[m] = basis of sites m..L-1
+    left = {0: (np.ones((1, 1)), np.zeros((1, 2), dtype=np.int64))}
+    right = {m: full_basis(L - m) for m in range(2, L + 1)}
+
+    def solve(b):
+        UL, qL = left[b]
+        UR, qR = right[b + 2]
+        dL, dR = UL.shape[1], UR.shape[1]
+        cols = []
+        for a in range(dL):
+            for s1 in range(4):
+                for s2 in range(4):
+                    for c in range(dR):
+                        if np.array_equal(qL[a] + LOCAL_Q[s1] + LOCAL_Q[s2] + qR[c], N):
+                            cols.append((a, s1, s2, c))
+        nR = UR.shape[0]
+        P = np.zeros((len(cfg), len(cols)))
+        for j, (a, s1, s2, c) in enumerate(cols):
+            vec = np.kron(np.kron(np.kron(UL[:, a], np.eye(4)[s1]), np.eye(4)[s2]), UR[:, c])
+            P[:, j] = vec[cfg]
+        HP = np.stack([fci_sigma(t, v, na, nb, P[:, j]) for j in range(P.shape[1])], axis=1)
+        Heff = P.T @ HP
+        Heff = 0.5 * (Heff + Heff.T)
+        w, Z = np.linalg.eigh(Heff)
+        psi = np.zeros((dL, 4, 4, dR))
+        for j, (a, s1, s2, c) in enumerate(cols):
+            psi[a, s1, s2, c] = Z[j, 0]
+        return w[0], psi, nR
+
+    def truncate_left(b, psi):
+        UL, qL = left[b]
+        dL = UL.shape[1]
+        M = psi.reshape(dL * 4, -1)
+        qrow = np.array([qL[a] + LOCAL_Q[s] for a in range(dL) for s in range(4)])
+        sectors = sorted({tuple(x) for x in qrow})
+        vecs, wts = [], []
+        for Q in sectors:
+            rows = np.where((qrow == Q).all(axis=1))[0]
+            rho = M[rows] @ M[rows].T
+            w, Z = np.linalg.eigh(0.5 * (rho + rho.T))
+            order = np.argsort(-w, kind="stable")
+            vecs.append((rows, Z[:, order]))
+            wts.append(w[order])
+        keep = truncation_keep(wts, D)
+        big = np.kron(UL, np.eye(4))
+        newU = np.stack([big[:, vecs[k][0]] @ vecs[k][1][:, i] for (k, i) in keep], axis=1)
+        newq = np.array([sectors[k] for (k, i) in keep], dtype=np.int64)
+        left[b + 1] = (newU, newq)
+
+    def truncate_right(b, psi):
+        UR, qR = right[b + 2]
+        dR = UR.shape[1]
+        M = psi.reshape(psi.shape[0] * 4, 4 * dR).T          # rows (s2, c)
+        qrow = np.array([LOCAL_Q[s] + qR[c] for s in range(4) for c in range(dR)])
+        sectors = sorted({tuple(x) for x in qrow})
+        vecs, wts = [], []
+        for Q in sectors:
+            rows = np.where((qrow == Q).all(axis=1))[0]
+            rho = M[rows] @ M[rows].T
+            w, Z = np.linalg.eigh(0.5 * (rho + rho.T))
+            order = np.argsort(-w, kind="stable")
+            vecs.append((rows, Z[:, order]))
+            wts.append(w[order])
+        keep = truncation_keep(wts, D)
+        big = np.kron(np.eye(4), UR)
+        newU = np.stack([big[:, vecs[k][0]] @ vecs[k][1][:, i] for (k, i) in keep], axis=1)
+        newq = np.array([sectors[k] for (k, i) in keep], dtype=np.int64)
+        right[b + 1] = (newU, newq)
+
+    energies = []
+    for _ in range(n_sweeps):
+        e = None
+        for b in range(0, L - 2):
+            e, psi, _ = solve(b)
+            truncate_left(b, psi)
+        for b in range(L - 2, 0, -1):
+            e, psi, _ = solve(b)
+            truncate_right(b, psi)
+        energies.append(float(e))
+    return energies

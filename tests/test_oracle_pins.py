@@ -256,3 +256,34 @@ def test_orbital_gradient_matches_finite_differences_and_vanishes_at_fci():
     w, U = O.fci_lowest(t, v, na, nb)
     G0 = O.orbital_gradient(t, v, na, nb, U[:, 0])
     assert np.abs(G0).max() < 1e-9
+
+
+def test_truncation_keep_reading():
+    """Kept states: largest weights first, ties by (sector, index); a near-degenerate group is
+    kept or dropped whole (fewer than D kept rather than splitting it)."""
+    w = [np.array([0.5, 0.1]), np.array([0.3, 0.1 + 1e-13]), np.array([0.0])]
+    assert O.truncation_keep(w, 10) == [(0, 0), (1, 0), (1, 1), (0, 1), (2, 0)]
+    assert O.truncation_keep(w, 2) == [(0, 0), (1, 0)]
+    # D = 3 would cut the (0.1, 0.1) pair of sectors 0 and 1: keep two instead
+    assert O.truncation_keep(w, 3) == [(0, 0), (1, 0)]
+    # exact ties are ordered by sector, then index
+    assert O.truncation_keep([np.array([0.2]), np.array([0.2, 0.2])], 5) == [(0, 0), (1, 0), (1, 1)]
+    # a degenerate group larger than D has to be split
+    assert O.truncation_keep([np.array([0.25, 0.25, 0.25, 0.25])], 2) == [(0, 0), (0, 1)]
+
+
+def test_oracle_dmrg_full_basis_equals_fci_and_truncation_is_variational():
+    """Plain two-site DMRG: at full bond dimension the sweep energy is the FCI energy (the
+    order of modes is then irrelevant, Sec. 2.2); truncated, it lies above FCI and does
+    not rise with D."""
+    L, na, nb = 6, 3, 3
+    t, v = I.synthetic_integrals(L, 57)
+    efci = O.fci_lowest(t, v, na, nb)[0][0]
+    e_full = O.dmrg_two_site(t, v, na, nb, 64, 2)
+    assert abs(e_full[-1] - efci) < 1e-10
+    e = {D: O.dmrg_two_site(t, v, na, nb, D, 2)[-1] for D in (4, 8, 16)}
+    assert all(x > efci - 1e-10 for x in e.values())
+    assert e[16] <= e[8] + 1e-10 and e[8] <= e[4] + 1e-10
+    # unbalanced spins, full basis at the centre cut of L = 5 (4^2 x 4^2 >= every sector)
+    t5, v5 = I.synthetic_integrals(5, 58)
+    assert abs(O.dmrg_two_site(t5, v5, 1, 3, 64, 1)[-1] - O.fci_lowest(t5, v5, 1, 3)[0][0]) < 1e-10
