@@ -82,3 +82,40 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
                         "-o", str(exe), lib, "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_problem_validation_without_a_device(lib):
+    """dmrg_build_ops rejects a bad problem statement before it touches the GPU."""
+    import numpy as np
+    from paper_2501_18263_gb300 import binding
+    L_ = binding.load_library(lib)
+
+    def status(L=4, na=2, nb=2, t=None, v=None, order=None, precision=0):
+        t = np.eye(L) if t is None else t
+        v = np.zeros((L, L, L, L)) if v is None else v
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        o = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+        p = binding._Problem(L, na, nb, binding._dp(t), binding._dp(v),
+                             o.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if o is not None else None,
+                             16, 0, precision, 0)
+        h = ctypes.c_void_p()
+        st = L_.dmrg_build_ops(ctypes.byref(p), None, ctypes.byref(h))
+        assert not h.value          # nothing is created on failure
+        return st, L_.dmrg_last_error().decode()
+
+    assert status(L=1)[0] == binding.ERR_ARG
+    assert status(L=65, t=np.eye(1), v=np.zeros((1, 1, 1, 1)))[0] == binding.ERR_ARG
+    assert status(na=5)[0] == binding.ERR_ARG
+    assert status(nb=-1)[0] == binding.ERR_ARG
+    assert status(precision=7)[0] == binding.ERR_ARG
+    bad = np.eye(4)
+    bad[1, 2] = np.nan
+    st, msg = status(t=bad)
+    assert st == binding.ERR_NONFINITE and "non-finite" in msg
+    vinf = np.zeros((4, 4, 4, 4))
+    vinf[0, 0, 0, 0] = np.inf
+    assert status(v=vinf)[0] == binding.ERR_NONFINITE
+    st, msg = status(order=[0, 1, 1, 3])
+    assert st == binding.ERR_ARG and "permutation" in msg
+    assert status(order=[0, 1, 2, 4])[0] == binding.ERR_ARG
