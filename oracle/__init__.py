@@ -438,16 +438,36 @@ def _block_configs_q(nsites):
     return q
 
 
-def dmrg_two_site(t, v, na, nb, D, n_sweeps):
+def right_blocks(L, right_bonds, right_sites, lowest=2):
+    """Initial right blocks for dmrg_two_site from a right-canonical MPS basis: for every
+    m = lowest..L, (V, q) with V[c, beta] the states of C_m over the configurations of sites
+    m..L-1 (right_basis) and q[beta] = (n_alpha, n_beta) of state beta."""
+    out = {}
+    for m in range(lowest, L + 1):
+        V = right_basis(L, m - 2, right_bonds, right_sites)
+        tab = right_bonds[m].as_array() if hasattr(right_bonds[m], "as_array") else right_bonds[m]
+        q = np.array([(int(a), int(b)) for (a, b, d) in tab for _ in range(int(d))], dtype=np.int64).reshape(-1, 2)
+        assert V.shape[1] == len(q)
+        out[m] = (V, q)
+    return out
+
+
+def dmrg_two_site(t, v, na, nb, D, n_sweeps, right_init=None, return_log=False):
     """Energies of n_sweeps two-site sweeps (left to right over bonds 0..L-3, then right to
     left over L-2..1; the energy of a sweep is the eigenvalue at its last step).
 
-    The initial right blocks are complete (every configuration of their sites), so the first
-    steps solve the problem exactly within the left basis kept so far.  At each bond the
-    effective Hamiltonian P^T H P (P embeds left basis x site x site x right basis into the
+    The initial right blocks are complete (every configuration of their sites) unless
+    right_init = {m: (V, q)} gives them (right_blocks()).  At each bond the effective
+    Hamiltonian P^T H P (P embeds left basis x site x site x right basis into the
     determinant space; H applied by fci_sigma) is built column by column and diagonalised
-    densely; the density matrix of the enlarged block is diagonalised per sector and the
-    states are kept by truncation_keep.
+    densely.  The reduced density matrix of the enlarged block that is truncated is
+    block diagonal over the sectors that psi occupies (a sector Q of that block with no
+    partner sector N - Q on the other side holds no part of psi and has no density-matrix
+    block); each block is diagonalised and the states are kept by truncation_keep.
+
+    With return_log, also returns one record per step: dict(sweep, bond, ltr, energy,
+    kept = [(n_alpha, n_beta, dim), ...] of the new block in sector order, discarded =
+    sum of the weights not kept).
     """
     L = t.shape[0]
     cfg = config_index(L, na, nb)
@@ -459,7 +479,11 @@ def dmrg_two_site(t, v, na, nb, D, n_sweeps):
 
     # blocks: left[k] = basis of sites 0..k-1 (k = 0..L-2), right[m] = basis of sites m..L-1
     left = {0: (np.ones((1, 1)), np.zeros((1, 2), dtype=np.int64))}
-    right = {m: full_basis(L - m) for m in range(2, L + 1)}
+    if right_init is None:
+        right = {m: full_basis(L - m) for m in range(2, L + 1)}
+    else:
+        right = {m: (np.asarray(V, dtype=np.float64), np.asarray(q, dtype=np.int64).reshape(-1, 2))
+                 for m, (V, q) in right_init.items()}
 
     def solve(b):
         UL, qL = left[b]
@@ -486,12 +510,10 @@ def dmrg_two_site(t, v, na, nb, D, n_sweeps):
             psi[a, s1, s2, c] = Z[j, 0]
         return w[0], psi, nR
 
-    def truncate_left(b, psi):
-        UL, qL = left[b]
-        dL = UL.shape[1]
-        M = psi.reshape(dL * 4, -1)
-        qrow = np.array([qL[a] + LOCAL_Q[s] for a in range(dL) for s in range(4)])
-        sectors = sorted({tuple(x) for x in qrow})
+    def keep_states(M, qrow, partner_q):
+        """Density-matrix blocks of the rows of M per occupied sector, kept states."""
+        occupied = {tuple(N - x) for x in partner_q}
+        sectors = sorted({tuple(x) for x in qrow} & occupied)
         vecs, wts = [], []
         for Q in sectors:
             rows = np.where((qrow == Q).all(axis=1))[0]
@@ -501,39 +523,58 @@ def dmrg_two_site(t, v, na, nb, D, n_sweeps):
             vecs.append((rows, Z[:, order]))
             wts.append(w[order])
         keep = truncation_keep(wts, D)
+        kept_set = set(keep)
+        disc = sum(max(0.0, float(wts[k][i])) for k in range(len(wts)) for i in range(len(wts[k]))
+                   if (k, i) not in kept_set)
+        counts = {}
+        for (k, i) in keep:
+            counts[k] = counts.get(k, 0) + 1
+        kept = [(int(sectors[k][0]), int(sectors[k][1]), counts[k]) for k in sorted(counts)]
+        return sectors, vecs, keep, kept, disc
+
+    def truncate_left(b, psi):
+        UL, qL = left[b]
+        UR, qR = right[b + 2]
+        dL = UL.shape[1]
+        M = psi.reshape(dL * 4, -1)
+        qrow = np.array([qL[a] + LOCAL_Q[s] for a in range(dL) for s in range(4)])
+        qcol = np.array([LOCAL_Q[s] + qR[c] for s in range(4) for c in range(UR.shape[1])])
+        sectors, vecs, keep, kept, disc = keep_states(M, qrow, qcol)
         big = np.kron(UL, np.eye(4))
         newU = np.stack([big[:, vecs[k][0]] @ vecs[k][1][:, i] for (k, i) in keep], axis=1)
         newq = np.array([sectors[k] for (k, i) in keep], dtype=np.int64)
-        left[b + 1] = (newU, newq)
+        # states sector by sector (the order a block basis is numbered in)
+        order = np.lexsort((np.arange(len(keep)), newq[:, 1], newq[:, 0]))
+        left[b + 1] = (newU[:, order], newq[order])
+        return kept, disc
 
     def truncate_right(b, psi):
+        UL, qL = left[b]
         UR, qR = right[b + 2]
         dR = UR.shape[1]
         M = psi.reshape(psi.shape[0] * 4, 4 * dR).T          # rows (s2, c)
         qrow = np.array([LOCAL_Q[s] + qR[c] for s in range(4) for c in range(dR)])
-        sectors = sorted({tuple(x) for x in qrow})
-        vecs, wts = [], []
-        for Q in sectors:
-            rows = np.where((qrow == Q).all(axis=1))[0]
-            rho = M[rows] @ M[rows].T
-            w, Z = np.linalg.eigh(0.5 * (rho + rho.T))
-            order = np.argsort(-w, kind="stable")
-            vecs.append((rows, Z[:, order]))
-            wts.append(w[order])
-        keep = truncation_keep(wts, D)
+        qcol = np.array([qL[a] + LOCAL_Q[s] for a in range(UL.shape[1]) for s in range(4)])
+        sectors, vecs, keep, kept, disc = keep_states(M, qrow, qcol)
         big = np.kron(np.eye(4), UR)
         newU = np.stack([big[:, vecs[k][0]] @ vecs[k][1][:, i] for (k, i) in keep], axis=1)
         newq = np.array([sectors[k] for (k, i) in keep], dtype=np.int64)
-        right[b + 1] = (newU, newq)
+        order = np.lexsort((np.arange(len(keep)), newq[:, 1], newq[:, 0]))
+        right[b + 1] = (newU[:, order], newq[order])
+        return kept, disc
 
-    energies = []
-    for _ in range(n_sweeps):
+    energies, log = [], []
+    for sw in range(n_sweeps):
         e = None
         for b in range(0, L - 2):
             e, psi, _ = solve(b)
-            truncate_left(b, psi)
+            kept, disc = truncate_left(b, psi)
+            log.append(dict(sweep=sw, bond=b, ltr=1, energy=float(e), kept=kept, discarded=disc))
         for b in range(L - 2, 0, -1):
             e, psi, _ = solve(b)
-            truncate_right(b, psi)
+            kept, disc = truncate_right(b, psi)
+            log.append(dict(sweep=sw, bond=b, ltr=0, energy=float(e), kept=kept, discarded=disc))
         energies.append(float(e))
+    if return_log:
+        return energies, log
     return energies

@@ -4,7 +4,7 @@ This module only draws numbers and lays them out; it holds none of the DMRG
 arithmetic (no Hamiltonian action, no operator algebra, no truncation).  Both the
 CUDA path and the CPU oracle consume exactly the arrays produced here.
 
-Conventions (all of them are interface conventions, restated in the design doc):
+Conventions (all of them are interface conventions):
 
 * Hamiltonian parameters follow the chemist convention
   H = sum_ij t_ij sum_s a+_is a_js + 1/2 sum_ijkl (ij|kl) sum_st a+_is a+_kt a_lt a_js,
@@ -302,3 +302,25 @@ def batched_problem(i):
     s = int(rng.choice(splits))
     D = int(rng.choice([256, 512, 1024]))
     return L, (L + s) // 2, (L - s) // 2, D, seed
+
+
+def complete_right_problem(L, na, nb, seed):
+    """Seeded bond-0 problem whose right blocks C_2 .. C_L are complete: every state of
+    site m (x) C_{m+1} is kept, rotated within its sector by a random orthogonal matrix
+    (QR of a Gaussian block).  psi is a seeded normalised vector of the bond-0 layout."""
+    rng = np.random.default_rng(seed)
+    rb = {L: Sectors([(0, 0)], [1])}
+    rs = {}
+    for m in range(L - 1, 1, -1):
+        enl = enlarged_layout(rb[m + 1])
+        q = list(enl.keys())
+        dims = [sum(d for (_, _, d) in enl[Q]) for Q in q]
+        rb[m] = Sectors(q, dims)
+        rs[m] = _isometries(rng, rb[m + 1], rb[m], "random")
+    lb = [Sectors([(0, 0)], [1])]
+    psi = []
+    for (QL, QR, r, c) in psi_block_shapes(lb[0], rb[2], na, nb):
+        psi.append((QL, QR, rng.standard_normal((r, c))))
+    nrm = math.sqrt(sum(float(np.sum(b * b)) for (_, _, b) in psi))
+    psi = [(a, b, blk / nrm) for (a, b, blk) in psi]
+    return BondProblem(L, na, nb, 0, lb, rb, [], rs, psi)

@@ -287,3 +287,60 @@ def test_oracle_dmrg_full_basis_equals_fci_and_truncation_is_variational():
     # unbalanced spins, full basis at the centre cut of L = 5 (4^2 x 4^2 >= every sector)
     t5, v5 = I.synthetic_integrals(5, 58)
     assert abs(O.dmrg_two_site(t5, v5, 1, 3, 64, 1)[-1] - O.fci_lowest(t5, v5, 1, 3)[0][0]) < 1e-10
+
+
+def _sectors(rows):
+    return I.Sectors([(a, b) for (a, b, _) in rows], [d for (_, _, d) in rows])
+
+
+def test_left_and_right_basis_row_order_by_hand():
+    """Which configuration each isometry row stands for, derived by hand from the stated
+    conventions (local states 0, beta, alpha, alpha beta; an enlarged sector lists its
+    sub-blocks by local state s = 0..3; configurations numbered with the leftmost site most
+    significant).  Left: B_2 of sites 0, 1 from a complete B_1; its sector (1, 1) has rows
+    s1 = 0 (site 0 doubly occupied), 1 (site 0 alpha), 2 (site 0 beta), 3 (site 0 empty),
+    i.e. configurations 3*4+0, 2*4+1, 1*4+2, 0*4+3.  Right: C_2 of sites 2, 3 from a complete
+    C_3; sector (1, 1) has rows s2 = 0..3 with site 3 in (1,1), (1,0), (0,1), (0,0), i.e.
+    configurations 0*4+3, 1*4+2, 2*4+1, 3*4+0."""
+    W = np.arange(1.0, 9.0).reshape(4, 2)
+    all4 = [(0, 0, 1), (0, 1, 1), (1, 0, 1), (1, 1, 1)]
+    left_bonds = [_sectors([(0, 0, 1)]), _sectors(all4), _sectors([(1, 1, 2)])]
+    left_sites = [{(a, b): np.ones((1, 1)) for (a, b, _) in all4}, {(1, 1): W}]
+    U = O.left_basis(left_bonds, left_sites)
+    expect = np.zeros((16, 2))
+    for r, cfg in enumerate((12, 9, 6, 3)):
+        expect[cfg] = W[r]
+    np.testing.assert_array_equal(U, expect)
+    right_bonds = {4: _sectors([(0, 0, 1)]), 3: _sectors(all4), 2: _sectors([(1, 1, 2)])}
+    right_sites = {3: {(a, b): np.ones((1, 1)) for (a, b, _) in all4}, 2: {(1, 1): W}}
+    V = O.right_basis(4, 0, right_bonds, right_sites)
+    expect = np.zeros((16, 2))
+    for r, cfg in enumerate((3, 6, 9, 12)):
+        expect[cfg] = W[r]
+    np.testing.assert_array_equal(V, expect)
+
+
+def test_oracle_dmrg_is_invariant_under_rotations_of_a_complete_initial_basis():
+    """Complete right blocks rotated within their sectors span the same spaces as the
+    plain configuration basis, so every step of the sweeps (energy, kept sectors,
+    discarded weight) is the same; a wrong row order or a transposed isometry in the
+    initial-basis path changes the spans and breaks this."""
+    L, na, nb, D = 6, 3, 2, 8
+    t, v = I.synthetic_integrals(L, 91)
+    bp = I.complete_right_problem(L, na, nb, seed=92)
+    init = O.right_blocks(L, bp.right_bonds, bp.right_sites)
+    e0, log0 = O.dmrg_two_site(t, v, na, nb, D, 2, return_log=True)
+    e1, log1 = O.dmrg_two_site(t, v, na, nb, D, 2, right_init=init, return_log=True)
+    assert len(log0) == len(log1) == 2 * (2 * L - 4)
+    for a, b in zip(log0, log1):
+        assert a["kept"] == b["kept"]
+        assert abs(a["energy"] - b["energy"]) < 1e-10
+        assert abs(a["discarded"] - b["discarded"]) < 1e-12
+    # the log's own invariants: at most D states kept, sectors ascending, discarded weight
+    # in [0, 1] and zero wherever nothing had to be dropped
+    for x in log0:
+        assert sum(d for (_, _, d) in x["kept"]) <= D
+        assert [q[:2] for q in x["kept"]] == sorted(q[:2] for q in x["kept"])
+        assert -1e-15 <= x["discarded"] <= 1.0
+    full = O.dmrg_two_site(t, v, na, nb, 4 ** 3, 1, return_log=True)[1]
+    assert all(abs(x["discarded"]) < 1e-14 for x in full)
