@@ -126,18 +126,22 @@ dmrg_status dmrg_sigma_ex(dmrg_handle* h, int32_t bond, const double* psi_dev, d
 dmrg_status dmrg_sigma_host(dmrg_handle* h, int32_t bond, const double* psi_host, double* sigma_host);
 
 /* Allocation-free variant of dmrg_sigma_host (the paper has no counterpart;
- * this is a library convenience).  For callers that may not allocate device
- * memory during the call -- for example while a CUDA graph is being captured,
- * or under a memory pool that must not grow -- psi and sigma are staged in a
- * device array built into the library (32 MiB, held by every device that loads
- * the library until the process exits) instead of a buffer allocated per call.
+ * this is a library convenience).  Some callers may not allocate device memory
+ * while they run: a service that sized its device memory once at start-up and
+ * may not grow it, or a caller whose device allocator belongs to someone else (a
+ * framework's memory pool, a fixed arena) and must not be entered from here.
+ * For them psi and sigma are staged in a device array built into the library
+ * (32 MiB, held by every device that loads the library until the process exits)
+ * instead of a buffer allocated per call.
  * Requirements and limits:
  *   - the bond must already be prepared (dmrg_prepare), which is where all of
- *     the handle's device memory is allocated; this call allocates nothing;
+ *     the handle's device memory is allocated; this call allocates nothing
+ *     (no cudaMalloc, no cudaMallocAsync, no allocating library routine);
  *   - psi_size <= 2097152 doubles, otherwise DMRG_ERR_ARG;
  *   - the handle's device must be current.  The first call on a device looks up
- *     the array's device address once; make that first call before any stream
- *     capture begins.
+ *     the array's device address (cudaGetSymbolAddress) once and keeps it.
+ * The call waits for its result (device-to-host copy) before it returns; its
+ * statuses are those of dmrg_sigma_host.
  * All calls share the one array and it keeps the last call's contents: calls
  * that overlap on the GPU (other threads, other handles on the same device)
  * race with each other and must be serialised by the caller. */
@@ -149,13 +153,42 @@ dmrg_status dmrg_sigma_host_noalloc(dmrg_handle* h, int32_t bond, const double* 
 dmrg_status dmrg_davidson(dmrg_handle* h, int32_t bond, double* psi_dev, double tol, int32_t max_iter,
                           double* energy, int32_t* iterations);
 
-/* n_sweeps full two-site sweeps (left-to-right then right-to-left) with bond
- * dimension D_schedule[s] (host, or NULL for problem->D); energies[s] (host)
- * receives the Davidson energy of the last step of sweep s.  Starts from the
- * loaded right-canonical basis at bond 0 if one was loaded, otherwise from a
- * seeded basis of kept product states. */
+/* n_sweeps full two-site sweeps (Sec. 2.1: the ALS sweep over neighbouring
+ * site pairs; Sec. 4.1 names its steps Diag_H, SVD, Ren_l / Ren_r, StVec):
+ * left to right over bonds 0..L-3, then right to left over bonds L-2..1, each
+ * step a Davidson solve at the bond followed by the density-matrix truncation
+ * to at most D_schedule[s] states (host, or NULL for problem->D) and the move
+ * of the wave function to the next bond.  energies[s] (host) receives the
+ * Davidson energy of the last step of sweep s.  Starts from the loaded
+ * right-canonical basis at bond 0 if one was loaded, otherwise from a seeded
+ * basis of kept product states.  Each Davidson solve stops when the residual
+ * 2-norm of the normalised Ritz vector is <= tol; on a split-BF16 handle the
+ * step whose energy is reported is refined with FP64 sigmas of its Ritz
+ * vector, and the other steps stop at the residual floor of the split-BF16
+ * sigma (about 1e-6 |E|).  Returns DMRG_ERR_NOCONV, with the energies
+ * written, when any step reached 100 iterations without either. */
 dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,
                        double* energies);
+
+/* dmrg_sweep with options: flags bit 0 = on a split-BF16 handle, refine every
+ * step with FP64 sigmas (not only the reported one); max_iter = Davidson
+ * iteration limit per step (<= 0: 100).  Other flag bits are rejected. */
+dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,
+                          double* energies, int32_t flags, int32_t max_iter);
+
+/* Per-step record of the last dmrg_sweep / dmrg_sweep_ex call (library-owned
+ * host tables, valid until the next call on the handle).
+ *   rows: double[n_steps * 8] = (sweep, bond, direction 1 = left to right /
+ *         0 = right to left, Davidson iterations, status, energy, final
+ *         residual 2-norm, discarded density-matrix weight), where status is
+ *         0 converged to tol, 1 stopped at the split-BF16 residual floor,
+ *         2 reached max_iter, 3 subspace exhausted (no new direction);
+ *   kept: int32[n_kept * 4] = (step index, n_alpha, n_beta, kept states) for
+ *         every sector of the block that the step's truncation produced, in
+ *         sector order (Sec. 2.1: the kept eigenvectors of the reduced density
+ *         matrix define the new block basis). */
+dmrg_status dmrg_sweep_log(dmrg_handle* h, int32_t* n_steps, const double** rows, int32_t* n_kept,
+                           const int32_t** kept);
 
 /* Wall seconds of the last dmrg_sweep call split by phase, in the categories of
  * the paper's timing breakdown (Sec. 4.1): seconds5[0] Tables (sigma plans and
@@ -183,8 +216,21 @@ dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi_
  * flops_stage1, flops_stage2 (algorithmic sigma flops), operator_bytes,
  * gemm_problems, gemm_segments, kernel launches of one FP64 sigma, then for the
  * split-BF16 plan: stage-1 tiles, stage-1 tile x K-stage count, stage-2 tiles,
- * stage-2 tile x K-stage count, X elements, BF16 plane bytes, 0, 0. */
+ * stage-2 tile x K-stage count, X elements, BF16 plane bytes, then
+ * [14] device allocations the handle has made since it was created (every
+ * cudaMallocAsync of the library on the handle's behalf; calls that allocate
+ * nothing leave it unchanged) and [15] the number of term chunks of one sigma
+ * (terms are cut into chunks so that the stage-1 intermediates fit under
+ * mem_cap_bytes). */
 dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out16);
+
+/* Code paths of the prepared bond's sigma plans (an implementation detail,
+ * reported so that tests can show which paths a case exercises): int64[8] =
+ * FP64 term chunks, split-BF16 term chunks, split-K parts of split-BF16 stage 2,
+ * stage-1 problems with several contributing fine blocks, stage-1 gathered-row
+ * problems, largest coarse L' dimension of psi, stage-2 problems spanning more
+ * than one 128-row tile, number of terms. */
+dmrg_status dmrg_plan_paths(dmrg_handle* h, int64_t* out8);
 
 /* Kernel timing with CUDA events on the handle's stream (this library's
  * kernels only).  mode = 1: reset counters and start; mode = 0: stop and write

@@ -18,8 +18,8 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOCONV, ERR_NONFINITE, ERR_STAT
 PREC_FP64, PREC_MIXED_BF16 = 0, 1
 
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
-           "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_stats",
-           "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
+           "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_ex", "dmrg_sweep_log", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_stats",
+           "dmrg_plan_paths", "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
            "dmrg_last_error"]
 SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
 PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "eigen", "gemm_bf16x", "split", "gemm_bf16x_stage1"]
@@ -61,9 +61,12 @@ def load_library(path: str | None = None):
         "dmrg_sigma_host_noalloc": ([vp, i32, dp, dp], ctypes.c_int),
         "dmrg_davidson": ([vp, i32, vp, f64, i32, dp, ip], ctypes.c_int),
         "dmrg_sweep": ([vp, i32, ip, f64, dp], ctypes.c_int),
+        "dmrg_sweep_ex": ([vp, i32, ip, f64, dp, i32, i32], ctypes.c_int),
+        "dmrg_sweep_log": ([vp, ip, ctypes.POINTER(dp), ip, ctypes.POINTER(ip)], ctypes.c_int),
         "dmrg_sweep_phases": ([vp, dp], ctypes.c_int),
         "dmrg_sigma_backward": ([vp, i32, vp, vp, vp, vp], ctypes.c_int),
         "dmrg_stats": ([vp, i64p], ctypes.c_int),
+        "dmrg_plan_paths": ([vp, i64p], ctypes.c_int),
         "dmrg_profile": ([vp, i32, dp], ctypes.c_int),
         "dmrg_batch_create": ([i32, ctypes.POINTER(vp), ip, ctypes.POINTER(vp)], ctypes.c_int),
         "dmrg_batch_sigma": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32], ctypes.c_int),
@@ -171,15 +174,39 @@ class Dmrg:
             self._check(st)
         return e.value, it.value
 
-    def sweep(self, n_sweeps, D_schedule=None, tol=1e-8):
+    def sweep(self, n_sweeps, D_schedule=None, tol=1e-8, refine_all=False, max_iter=100, check=True):
+        """Energies of n_sweeps sweeps; with check=False a DMRG_ERR_NOCONV status is kept in
+        self.last_status instead of raised (the energies are written either way)."""
         e = np.zeros(n_sweeps)
         Ds = None
         if D_schedule is not None:
             Ds = np.ascontiguousarray(D_schedule, dtype=np.int32)
-        self._check(self.lib.dmrg_sweep(self.h, n_sweeps,
-                                        Ds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if Ds is not None else None,
-                                        float(tol), _dp(e)))
+        st = self.lib.dmrg_sweep_ex(self.h, n_sweeps,
+                                    Ds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if Ds is not None else None,
+                                    float(tol), _dp(e), 1 if refine_all else 0, int(max_iter))
+        self.last_status = st
+        if check or st not in (OK, ERR_NOCONV):
+            self._check(st)
         return e
+
+    def sweep_log(self):
+        """Per-step record of the last sweep call: a list of dicts (sweep, bond, ltr, iters,
+        status, energy, rnorm, discarded, kept = [(n_alpha, n_beta, dim), ...])."""
+        n = ctypes.c_int32()
+        rows = ctypes.POINTER(ctypes.c_double)()
+        nk = ctypes.c_int32()
+        kept = ctypes.POINTER(ctypes.c_int32)()
+        self._check(self.lib.dmrg_sweep_log(self.h, ctypes.byref(n), ctypes.byref(rows), ctypes.byref(nk),
+                                            ctypes.byref(kept)))
+        R = np.ctypeslib.as_array(rows, shape=(n.value * 8,)).reshape(-1, 8).copy() if n.value else np.zeros((0, 8))
+        K = np.ctypeslib.as_array(kept, shape=(nk.value * 4,)).reshape(-1, 4).copy() if nk.value else \
+            np.zeros((0, 4), np.int32)
+        out = []
+        for k, r in enumerate(R):
+            out.append(dict(sweep=int(r[0]), bond=int(r[1]), ltr=int(r[2]), iters=int(r[3]), status=int(r[4]),
+                            energy=float(r[5]), rnorm=float(r[6]), discarded=float(r[7]),
+                            kept=[(int(a), int(b), int(c)) for (_, a, b, c) in K[K[:, 0] == k]]))
+        return out
 
     def sweep_phases(self):
         """Wall seconds of the last sweep call per phase (Tables, Diag_H, SVD, Ren, StVec)."""
@@ -205,7 +232,14 @@ class Dmrg:
         self._check(self.lib.dmrg_stats(self.h, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         keys = ["psi_size", "n_terms", "flops_stage1", "flops_stage2", "op_bytes", "gemm_problems",
                 "gemm_segments", "launches_per_sigma", "mix_tiles1", "mix_steps1", "mix_tiles2", "mix_steps2",
-                "mix_x_elems", "mix_plane_bytes"]
+                "mix_x_elems", "mix_plane_bytes", "device_allocs", "chunks"]
+        return dict(zip(keys, (int(x) for x in o)))
+
+    def plan_paths(self):
+        o = np.zeros(8, dtype=np.int64)
+        self._check(self.lib.dmrg_plan_paths(self.h, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        keys = ["chunks_fp64", "chunks_mixed", "split_k_parts", "stage1_multi_block", "stage1_gathered",
+                "max_coarse_rows", "stage2_multi_row_tile", "terms"]
         return dict(zip(keys, (int(x) for x in o)))
 
 

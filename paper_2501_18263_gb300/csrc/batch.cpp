@@ -41,29 +41,11 @@ struct dmrg_batch {
 
 namespace {
 
-dmrg_status fail(dmrg_status s, const std::string& m) {
-  dmrg_internal_set_error(m.c_str());
-  return s;
-}
+dmrg_status fail(dmrg_status s, const std::string& m) { return dmrg_internal_fail(s, m); }
 
 template <class F>
 dmrg_status guard(F&& f) {
-  try {
-    dmrg_internal_set_error("");
-    return f();
-  } catch (const dmrg::CudaError& e) {
-    return fail(DMRG_ERR_CUDA, e.what());
-  } catch (const dmrg::OomError& e) {
-    return fail(DMRG_ERR_OOM, e.what());
-  } catch (const dmrg::TimeoutError& e) {
-    return fail(DMRG_ERR_TIMEOUT, e.what());
-  } catch (const std::bad_alloc&) {
-    return fail(DMRG_ERR_OOM, "host allocation failed");
-  } catch (const std::exception& e) {
-    return fail(DMRG_ERR_ARG, e.what());
-  } catch (...) {
-    return fail(DMRG_ERR_STATE, "unknown error");
-  }
+  return dmrg_internal_guard(std::forward<F>(f));
 }
 
 // one plan made of the given plans of several executors: problems, segments and

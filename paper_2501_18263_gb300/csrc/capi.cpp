@@ -7,10 +7,6 @@
 #include <stdexcept>
 #include <string>
 
-#include "../../include/dmrg_gb300.h"
-#include "core/core.h"
-#include "exec_errors.h"
-
 #include <cuda_runtime.h>
 
 #include "capi_internal.h"
@@ -18,29 +14,11 @@
 namespace {
 thread_local std::string g_err;
 
-dmrg_status fail(dmrg_status s, const std::string& m) {
-  g_err = m;
-  return s;
-}
+dmrg_status fail(dmrg_status s, const std::string& m) { return dmrg_internal_fail(s, m); }
 
 template <class F>
 dmrg_status guard(F&& f) {
-  try {
-    g_err.clear();
-    return f();
-  } catch (const dmrg::CudaError& e) {
-    return fail(DMRG_ERR_CUDA, e.what());
-  } catch (const dmrg::OomError& e) {
-    return fail(DMRG_ERR_OOM, e.what());
-  } catch (const dmrg::TimeoutError& e) {
-    return fail(DMRG_ERR_TIMEOUT, e.what());
-  } catch (const std::bad_alloc&) {
-    return fail(DMRG_ERR_OOM, "host allocation failed");
-  } catch (const std::exception& e) {
-    return fail(DMRG_ERR_ARG, e.what());
-  } catch (...) {
-    return fail(DMRG_ERR_STATE, "unknown error");
-  }
+  return dmrg_internal_guard(std::forward<F>(f));
 }
 
 bool finite(const double* p, size_t n) {
@@ -49,13 +27,7 @@ bool finite(const double* p, size_t n) {
   return true;
 }
 
-// a bounded device-side wait that gave up leaves a nonzero error word
-dmrg_status check_device(dmrg_handle* h) {
-  const int code = h->eng->exec()->device_error();
-  if (code == 9) return fail(DMRG_ERR_NOCONV, "the symmetric eigensolver did not converge");
-  if (code) return fail(DMRG_ERR_TIMEOUT, "a tensor-core pipeline wait gave up; destroy the handle");
-  return DMRG_OK;
-}
+dmrg_status check_device(dmrg_handle* h) { return dmrg_internal_check_device(h); }
 
 dmrg_status ensure_bond(dmrg_handle* h, int bond) {
   if (bond < 0 || bond > h->L - 2) return fail(DMRG_ERR_ARG, "bond out of range");
@@ -256,12 +228,13 @@ dmrg_status dmrg_davidson(dmrg_handle* h, int32_t bond, double* psi, double tol,
   });
 }
 
-dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,
-                       double* energies) {
+dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,
+                          double* energies, int32_t flags, int32_t max_iter) {
   return guard([&]() -> dmrg_status {
     if (!h || n_sweeps <= 0) return fail(DMRG_ERR_ARG, "bad arguments");
     if (h->L < 3) return fail(DMRG_ERR_ARG, "sweeps need L >= 3");
     if (!(tol > 0)) return fail(DMRG_ERR_ARG, "tol must be positive");
+    if (flags & ~1) return fail(DMRG_ERR_ARG, "unknown sweep flags");
     std::vector<int> D(n_sweeps);
     for (int s = 0; s < n_sweeps; ++s) {
       D[s] = D_schedule ? D_schedule[s] : h->eng->problem().D;
@@ -270,13 +243,48 @@ dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedu
     if (h->right_loaded > 2 && h->any_loaded && !h->eng->right_block(2).valid)
       return fail(DMRG_ERR_ARG, "a partially loaded basis must reach site 2 for sweeps");
     h->eng->set_D(D[0]);
-    std::vector<double> e = h->eng->run_sweeps(n_sweeps, D.data(), tol);
+    std::vector<double> e = h->eng->run_sweeps(n_sweeps, D.data(), tol, flags, max_iter > 0 ? max_iter : 100);
     h->eng->exec()->sync();
     if (energies)
       for (int s = 0; s < n_sweeps; ++s) energies[s] = e[s];
-    if (check_device(h) != DMRG_OK) return DMRG_ERR_TIMEOUT;
+    dmrg_status ds = check_device(h);
+    if (ds != DMRG_OK) return ds;
     for (double x : e)
       if (!std::isfinite(x)) return fail(DMRG_ERR_NONFINITE, "non-finite energy");
+    int nc = 0;
+    for (const auto& lg : h->eng->sweep_log_)
+      if (lg.status == 2) ++nc;
+    if (nc)
+      return fail(DMRG_ERR_NOCONV, std::to_string(nc) + " sweep step(s) reached max_iter without convergence "
+                                   "(energies are written; dmrg_sweep_log lists the steps)");
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,
+                       double* energies) {
+  return dmrg_sweep_ex(h, n_sweeps, D_schedule, tol, energies, 0, 100);
+}
+
+dmrg_status dmrg_sweep_log(dmrg_handle* h, int32_t* n_steps, const double** rows, int32_t* n_kept,
+                           const int32_t** kept) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !n_steps || !rows || !n_kept || !kept) return fail(DMRG_ERR_ARG, "null argument");
+    const auto& lg = h->eng->sweep_log_;
+    h->log_rows.clear();
+    h->log_kept.clear();
+    for (size_t k = 0; k < lg.size(); ++k) {
+      const auto& x = lg[k];
+      for (double v : {double(x.sweep), double(x.bond), double(x.ltr), double(x.iters), double(x.status), x.energy,
+                       x.rnorm, x.discarded})
+        h->log_rows.push_back(v);
+      for (size_t j = 0; j + 2 < x.kept.size(); j += 3)
+        for (int v : {int(k), x.kept[j], x.kept[j + 1], x.kept[j + 2]}) h->log_kept.push_back(v);
+    }
+    *n_steps = int32_t(lg.size());
+    *rows = h->log_rows.data();
+    *n_kept = int32_t(h->log_kept.size() / 4);
+    *kept = h->log_kept.data();
     return DMRG_OK;
   });
 }
@@ -317,8 +325,25 @@ dmrg_status dmrg_stats(dmrg_handle* h, int64_t* o) {
     o[11] = s.mix_steps2;
     o[12] = s.mix_x_elems;
     o[13] = s.mix_plane_bytes;
-    o[14] = 0;
-    o[15] = 0;
+    o[14] = h->eng->exec()->alloc_count();
+    o[15] = s.n_chunks;
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_plan_paths(dmrg_handle* h, int64_t* o) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !o) return fail(DMRG_ERR_ARG, "null argument");
+    if (h->eng->bond() < 0) return fail(DMRG_ERR_ARG, "no bond prepared");
+    const dmrg::BondStats& s = h->eng->stats();
+    o[0] = s.n_chunks;
+    o[1] = s.mix_chunks;
+    o[2] = s.mix_parts;
+    o[3] = s.mix_mode2;
+    o[4] = s.mix_mode3;
+    o[5] = s.max_rows;
+    o[6] = s.mix_multirow;
+    o[7] = s.n_terms;
     return DMRG_OK;
   });
 }

@@ -127,6 +127,12 @@ struct BondStats {
   int launches_per_sigma = 0;
   // split-BF16 plan: tiles and K stages (32 wide) of stage 1 / stage 2, X elements, plane bytes
   int64_t mix_tiles1 = 0, mix_steps1 = 0, mix_tiles2 = 0, mix_steps2 = 0, mix_x_elems = 0, mix_plane_bytes = 0;
+  // which code paths the plan uses: term chunks (FP64 / split-BF16), split-K parts
+  // of stage 2, stage-1 problems with several contributing fine blocks (mode 2) and
+  // gathered-row problems (mode 3), the largest coarse L' dimension of psi, and the
+  // stage-2 problems with more than one 128-row tile
+  int64_t n_chunks = 0, mix_chunks = 0, mix_parts = 0, mix_mode2 = 0, mix_mode3 = 0, max_rows = 0,
+          mix_multirow = 0;
 };
 
 class Engine {
@@ -155,12 +161,17 @@ class Engine {
   void sigma_precision(const double* psi, double* sig, int precision);
   void diagonal(double* d);                                    // diag of H_eff (device)
 
-  // Davidson on the current bond; psi in/out (device).  Returns energy.
+  // Davidson on the current bond; psi in/out (device).  Returns energy.  Sets
+  // last_status: 0 converged (residual <= tol; for the split-BF16 sigma with
+  // refine = 1, after an FP64 refinement), 1 stopped at the residual floor of the
+  // split-BF16 sigma (refine = 0 only), 2 max_iter reached, 3 no new direction
+  // (the subspace is invariant).
   double davidson(double* psi, double tol, int max_iter, int max_sub, int* iters_out, int refine);
 
-  // sweeps
+  // sweeps.  flags bit 0: FP64 refinement at every step of a split-BF16 sweep
+  // (otherwise only at the step whose energy is reported)
   void init_sweep_state();
-  std::vector<double> run_sweeps(int n, const int* Dsched, double tol);
+  std::vector<double> run_sweeps(int n, const int* Dsched, double tol, int flags = 0, int max_iter = 100);
 
   // expose a block operator for tests
   const Block& left_block(int n) const { return lb_[n]; }
@@ -171,7 +182,14 @@ class Engine {
 
   double last_energy = 0.0;
   double last_rnorm = 0.0;
-  struct StepLog { int sweep, bond, ltr; double energy; int iters; };
+  int last_status = 0;
+  struct StepLog {
+    int sweep, bond, ltr;
+    double energy;
+    int iters, status;
+    double rnorm, discarded;
+    std::vector<int> kept;   // sectors of the new block: (n_alpha, n_beta, dim) triples
+  };
   std::vector<StepLog> sweep_log_;
   // wall seconds of the last run_sweeps call per phase (Sec. 4.1 categories):
   // 0 Tables (sigma plans), 1 Diag_H (Davidson), 2 SVD (density matrices,
@@ -256,7 +274,7 @@ class Engine {
   void renormalize(bool left, const Enlarged& E, const OpSet& eops, const Iso& iso, Block& out);
   void build_sigma_plan();
   void free_bond();
-  void truncate_and_move(bool left_to_right, int D, double* trunc_w);
+  void truncate_and_move(bool left_to_right, int D, double* trunc_w, std::vector<int>* kept = nullptr);
 };
 
 // site matrices

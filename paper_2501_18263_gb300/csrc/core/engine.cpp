@@ -189,6 +189,7 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
   int refines = 0, last_refine = -100;
   double best = 1e300;
   int best_it = 0;
+  int status = 2;
   for (;; ++it) {
     ex_->ritz(Hs, lds, m, theta, y);
     if (it > 0) {
@@ -210,9 +211,24 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
       best_it = it;
     }
     if (!mixed) {
-      if (rnorm <= tol) break;
+      if (rnorm <= tol) {
+        status = 0;
+        break;
+      }
+      // split-BF16 sigma without refinement: its residual cannot fall below the
+      // level that precision resolves; stop there instead of running to max_iter
+      if (prec != 0) {
+        const double floor_m = 1e-6 * std::max(1.0, std::fabs(th));
+        if (rnorm <= floor_m || it - best_it >= 8) {
+          status = 1;
+          break;
+        }
+      }
     } else {
-      if (refines > 0 && rnorm <= tol) break;
+      if (refines > 0 && rnorm <= tol) {
+        status = 0;
+        break;
+      }
       const double floor_m = 1e-6 * std::max(1.0, std::fabs(th));
       const bool stalled = it - best_it >= 8;
       if ((rnorm <= std::max(tol, floor_m) || stalled) && it - last_refine >= 4 && refines < 8) {
@@ -275,7 +291,10 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
     ex_->mdot(t, n, 1, t, n, 1, n, nrm2, 1);
     double tn2;
     ex_->d2h(&tn2, nrm2, sizeof(double));
-    if (!(tn2 > 1e-28)) break;  // no new direction
+    if (!(tn2 > 1e-28)) {  // no new direction
+      status = 3;
+      break;
+    }
     ex_->normalize(t, n, nrm2);
     ex_->d2d(V + int64_t(m) * n, t, n * sizeof(double));
     apply(V + int64_t(m) * n, W + int64_t(m) * n, prec);
@@ -290,6 +309,7 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
   if (iters_out) *iters_out = it + 1;
   last_energy = th;
   last_rnorm = rnorm;
+  last_status = status;
   return th;
 }
 
@@ -332,7 +352,7 @@ std::vector<int> select_kept(const std::vector<std::vector<double>>& w, int D, d
 
 }  // namespace
 
-void Engine::truncate_and_move(bool ltr, int D, double* trunc_w) {
+void Engine::truncate_and_move(bool ltr, int D, double* trunc_w, std::vector<int>* kept_out) {
   const int b = bond_;
   const Enlarged& E = ltr ? EL_ : ER_;
   const int nc = int(E.coarse.q.size());
@@ -419,6 +439,14 @@ void Engine::truncate_and_move(bool ltr, int D, double* trunc_w) {
       kk.push_back(k);
     }
   out.finalize();
+  if (kept_out) {
+    kept_out->clear();
+    for (size_t k = 0; k < out.q.size(); ++k) {
+      kept_out->push_back(out.q[k].a);
+      kept_out->push_back(out.q[k].b);
+      kept_out->push_back(out.dim[k]);
+    }
+  }
   Iso& iso = ltr ? liso_[b] : riso_[b + 1];
   std::vector<const double*> nulls(out.q.size(), nullptr);
   set_iso(ex_, iso, out, krow, nulls, true);
@@ -701,7 +729,7 @@ void Engine::tick(int k) {
   t_last_ = t;
 }
 
-std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol) {
+std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol, int flags, int max_iter) {
   const int L = P_.L;
   if (L < 3) throw std::runtime_error("sweeps need L >= 3");
   if (!psi_cur_ || bond_ != 0) init_sweep_state();
@@ -711,24 +739,23 @@ std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol) {
   ex_->sync();
   t_last_ = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
   timing_ = true;
+  const bool refine_all = (flags & 1) != 0;
   for (int s = 0; s < nsw; ++s) {
     const int D = Dsched ? Dsched[s] : P_.D;
-    double e = 0.0, tw = 0.0;
+    double e = 0.0;
     int iters = 0;
-    // mixed precision: FP64 residual refinement only where the sweep energy is
-    // reported (last step); elsewhere the split-BF16 eigenvector is kept
-    for (int b = 0; b <= L - 3; ++b) {   // left to right
-      e = davidson(psi_cur_, tol, 100, 24, &iters, 0);
+    // split-BF16 sigma: FP64 residual refinement where the sweep energy is
+    // reported (the last step), and at every step with refine_all; the other
+    // steps stop at the split-BF16 residual floor
+    auto step = [&](int b, int ltr, int refine) {
+      e = davidson(psi_cur_, tol, max_iter, 24, &iters, refine);
       tick(1);
-      sweep_log_.push_back({s, b, 1, e, iters});
-      truncate_and_move(true, D, &tw);
-    }
-    for (int b = L - 2; b >= 1; --b) {   // right to left
-      e = davidson(psi_cur_, tol, 100, 24, &iters, b == 1 ? 1 : 0);
-      tick(1);
-      sweep_log_.push_back({s, b, 0, e, iters});
-      truncate_and_move(false, D, &tw);
-    }
+      StepLog lg{s, b, ltr, e, iters, last_status, last_rnorm, 0.0, {}};
+      truncate_and_move(ltr != 0, D, &lg.discarded, &lg.kept);
+      sweep_log_.push_back(std::move(lg));
+    };
+    for (int b = 0; b <= L - 3; ++b) step(b, 1, refine_all ? 1 : 0);           // left to right
+    for (int b = L - 2; b >= 1; --b) step(b, 0, (refine_all || b == 1) ? 1 : 0);  // right to left
     E.push_back(e);
   }
   timing_ = false;

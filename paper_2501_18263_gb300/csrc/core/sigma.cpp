@@ -203,7 +203,8 @@ void Engine::build_sigma_plan() {
     for (size_t k = 0; k < xl[n].size(); ++k) xidx[n][xl[n][k].iT] = int(k);
 
   // chunk terms so that X fits under the scratch cap
-  const int64_t xcap = std::max<int64_t>(int64_t(1) << 24, P_.mem_cap ? int64_t(P_.mem_cap / 16 / sizeof(double)) : int64_t(1) << 28);
+  const int64_t xcap = P_.mem_cap ? std::max<int64_t>(int64_t(1) << 14, int64_t(P_.mem_cap / 16 / sizeof(double)))
+                                  : int64_t(1) << 28;
   std::vector<std::pair<size_t, size_t>> ranges;
   {
     size_t s = 0;
@@ -218,6 +219,9 @@ void Engine::build_sigma_plan() {
     }
     ranges.push_back({s, T.size()});
   }
+  st_.n_chunks = int64_t(ranges.size());
+  for (size_t i = 0; i < EL_.coarse.q.size(); ++i)
+    if (psi_off_[i] >= 0) st_.max_rows = std::max<int64_t>(st_.max_rows, EL_.coarse.dim[i]);
   int64_t xmax = 0;
   for (auto& rg : ranges) {
     int64_t a = 0;
@@ -544,7 +548,7 @@ void Engine::build_sigma_plan() {
       xmsize[n] = o;
     }
     // one X buffer for all terms unless it exceeds the cap (2 bytes per element)
-    const int64_t xcap_m = P_.mem_cap ? std::max<int64_t>(int64_t(3) << 24, int64_t(P_.mem_cap / 4))
+    const int64_t xcap_m = P_.mem_cap ? std::max<int64_t>(int64_t(3) << 14, int64_t(P_.mem_cap / 4))
                                       : int64_t(3) << 33;
     std::vector<std::pair<size_t, size_t>> mranges;
     {
@@ -761,6 +765,9 @@ void Engine::build_sigma_plan() {
       };
       count(P1, S1, st_.mix_tiles1, st_.mix_steps1);
       count(P2, S2, st_.mix_tiles2, st_.mix_steps2);
+      for (const MixProb& q : P1) (q.mode == 2 ? st_.mix_mode2 : st_.mix_mode3) += 1;
+      for (const MixProb& q : P2)
+        if (q.M > 128) st_.mix_multirow += 1;
       Chunk ch;
       ch.plan1 = P1.empty() ? -1 : ex_->mix_plan_g(P1, S1, bcol, ccol, acol);
       ch.plan2 = ex_->mix_plan(P2, S2);
@@ -792,6 +799,8 @@ void Engine::build_sigma_plan() {
       }
       mplan_hl_ = P3.empty() ? -1 : ex_->mix_plan(P3, S3);
     }
+    st_.mix_chunks = int64_t(mranges.size());
+    st_.mix_parts = nparts_;
     mixed_ready_ = true;
   }
 

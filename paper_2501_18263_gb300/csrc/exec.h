@@ -115,6 +115,8 @@ class Exec {
  public:
   virtual ~Exec() {}
   virtual void* alloc(size_t bytes) = 0;
+  // number of device allocations made so far (alloc calls, plan uploads included)
+  virtual int64_t alloc_count() const = 0;
   virtual void release(void* p) = 0;
   virtual void zero(void* p, size_t bytes) = 0;
   virtual void h2d(void* d, const void* h, size_t bytes) = 0;

@@ -693,8 +693,10 @@ class CudaExec : public Exec {
     cudaFree(part_);
     cudaFree(err_);
   }
+  int64_t alloc_count() const override { return n_alloc_; }
   void* alloc(size_t b) override {
     void* p = nullptr;
+    ++n_alloc_;
     cudaError_t e = cudaMallocAsync(&p, b ? b : 8, st_);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -1025,6 +1027,7 @@ class CudaExec : public Exec {
   cudaStream_t st_;
   int prec_;
   int dev_ = 0, nsm_ = 148;
+  int64_t n_alloc_ = 0;
   double* part_ = nullptr;
   std::vector<Plan> plans_;
 };

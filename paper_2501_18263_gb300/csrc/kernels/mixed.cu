@@ -15,8 +15,8 @@
 // rows x 16 bytes per core matrix, the K groups of an 8-row group contiguous), so
 // the slice of one plane that a stage needs is one contiguous run of at most 512
 // bytes per 8-row group, moved by cp.async.bulk straight into the canonical
-// no-swizzle K-major shared-memory layout.  A ring of four stages is guarded by
-// mbarriers (the full barriers count the copies' bytes); every wait is bounded
+// no-swizzle K-major shared-memory layout.  A ring of STAGES (three) stages is
+// guarded by mbarriers (the full barriers count the copies' bytes); every wait is bounded
 // and sets an error word instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>

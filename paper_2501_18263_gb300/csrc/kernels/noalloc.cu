@@ -2,17 +2,16 @@
 // allocation.  dmrg_sigma_host stages psi and sigma in a device buffer that it
 // allocates on every call; this variant stages them in a file-scope device
 // array instead, for callers that must not allocate device memory while they
-// run (for example code that is being captured into a CUDA graph, or that runs
-// under a memory pool it may not grow).
+// run: a service that sized its device memory once at start-up and may not
+// grow it afterwards, or a caller whose allocator is owned by someone else
+// (a framework's memory pool, a fixed arena) and must not be entered from here.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <mutex>
 #include <string>
 
-#include "../../../include/dmrg_gb300.h"
 #include "../capi_internal.h"
-#include "../exec_errors.h"
 
 namespace {
 
@@ -25,17 +24,13 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};
 
-dmrg_status fail(dmrg_status s, const std::string& m) {
-  dmrg_internal_set_error(m.c_str());
-  return s;
-}
+dmrg_status fail(dmrg_status s, const std::string& m) { return dmrg_internal_fail(s, m); }
 
 }  // namespace
 
 extern "C" dmrg_status dmrg_sigma_host_noalloc(dmrg_handle* h, int32_t bond, const double* psi_host,
                                                double* sigma_host) {
-  try {
-    dmrg_internal_set_error("");
+  return dmrg_internal_guard([&]() -> dmrg_status {
     if (!h || !psi_host || !sigma_host) return fail(DMRG_ERR_ARG, "null argument");
     if (h->eng->bond() != bond)
       return fail(DMRG_ERR_ARG, "bond not prepared: call dmrg_prepare for this bond first");
@@ -64,16 +59,7 @@ extern "C" dmrg_status dmrg_sigma_host_noalloc(dmrg_handle* h, int32_t bond, con
     ex->h2d(base, psi_host, size_t(n) * sizeof(double));
     h->eng->sigma_precision(base, base + kMaxPsi, h->eng->problem().precision);
     ex->d2h(sigma_host, base + kMaxPsi, size_t(n) * sizeof(double));
-    // a bounded wait inside the tensor-core kernel that gave up leaves a nonzero word
-    if (ex->device_error()) return fail(DMRG_ERR_TIMEOUT, "a tensor-core pipeline wait gave up; destroy the handle");
-    return DMRG_OK;
-  } catch (const dmrg::CudaError& e) {
-    return fail(DMRG_ERR_CUDA, e.what());
-  } catch (const dmrg::OomError& e) {
-    return fail(DMRG_ERR_OOM, e.what());
-  } catch (const std::exception& e) {
-    return fail(DMRG_ERR_ARG, e.what());
-  } catch (...) {
-    return fail(DMRG_ERR_STATE, "unknown error");
-  }
+    // the same device status mapping as every other entry point
+    return dmrg_internal_check_device(h);
+  });
 }

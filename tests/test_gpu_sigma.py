@@ -1,7 +1,8 @@
 """GPU sigma (FP64 path) against the oracle's projected sigma P H P psi.
 
-Bar: integer sector tables bit-exact; sigma within relative error 1e-10
-(normwise, ||s_gpu - s_oracle|| / ||s_oracle||).
+Bar: integer sector tables bit-exact; sigma within relative error 1e-10, both
+normwise (||s_gpu - s_oracle|| / ||s_oracle||) and element-wise in every sector
+block (max |s_gpu - s_oracle| <= 1e-10 max |s_oracle| within the block).
 """
 import numpy as np
 import pytest
@@ -9,7 +10,7 @@ import pytest
 import oracle as O
 from paper_2501_18263_gb300 import binding as B
 from paper_2501_18263_gb300 import inputs as I
-from gpu_util import rel, stream, to_dev
+from gpu_util import assert_blocks, rel, stream, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +42,7 @@ def _run(L, na, nb, D, bond, seed, kind, precision=B.PREC_FP64):
     sig = psi.new_empty(psi.shape)
     d.sigma(bond, psi.data_ptr(), sig.data_ptr())
     ref = B.pack_psi(O.projected_sigma(t, v, na, nb, bp, bp.psi))
+    d.lay = lay
     return d, bp, sig.cpu().numpy(), ref
 
 
@@ -48,6 +50,7 @@ def _run(L, na, nb, D, bond, seed, kind, precision=B.PREC_FP64):
 def test_sigma_fp64_matches_oracle(case):
     d, bp, sig, ref = _run(*case)
     assert rel(sig, ref) < 1e-10
+    assert_blocks(sig, ref, d.lay, 1e-10)
     st = d.stats()
     assert st["psi_size"] == len(ref)
     assert st["flops_stage1"] + st["flops_stage2"] > 0
