@@ -199,18 +199,53 @@ dmrg_status dmrg_sweep_log(dmrg_handle* h, int32_t* n_steps, const double** rows
  * phases add up to the sweep's wall time.  seconds5 is host memory. */
 dmrg_status dmrg_sweep_phases(dmrg_handle* h, double* seconds5);
 
-/* Reduced density matrices at the prepared bond (Sec. 2.2 uses them for
- * orbital rotations): with x = lam_dev, y = psi_dev (device, psi_size doubles)
- *   g1[i*L+j]             += <x| sum_s a+_is a_js |y>
- *   g2[((i*L+j)*L+k)*L+l] += <x| sum_st a+_is a+_kt a_lt a_js |y>
- * so that dE/dt = g1 and dE/dv = g2/2 for x = y = the normalised eigenvector.
- * g1, g2 are device buffers (L^2 and L^4 doubles).
- * NOT IMPLEMENTED in this version of the library: the call checks its
- * arguments and the bond index, then returns DMRG_ERR_ARG with the message
- * "dmrg_sigma_backward: not implemented in this version of the library"; it
- * prepares nothing and writes nothing. */
+/* Adjoint of the sigma step (the differentiation form; Sec. 2.2 uses the
+ * density matrices it yields for the orbital rotations c~+ = U c+ of mode
+ * optimisation).  With F = <lam| H_eff(t, v) |psi> at `bond` for the handle's
+ * fixed MPS basis (psi_dev, lam_dev: device, psi_size doubles in the layout of
+ * dmrg_layout), the call ADDS to the device buffers
+ *   g1[i*L + j]             (L^2 doubles): dF/dt_ij, symmetrised over i <-> j;
+ *   g2[((i*L + j)*L + k)*L + l]  (L^4 doubles): 2 dF/dv_ijkl, symmetrised over the
+ *                           eight index permutations of a real (ij|kl);
+ * in the caller's orbital numbering, i.e. for symmetric t and 8-fold symmetric v
+ *   F = sum_ij t_ij g1_ij + 1/2 sum_ijkl v_ijkl g2_ijkl   (F is linear in t, v).
+ * For lam = psi = the normalised eigenvector, g1 is the one-particle density
+ * matrix  <E_ij> = sum_s <a+_is a_js>  (symmetric) and g2 the two-particle one
+ * <sum_st a+_is a+_kt a_lt a_js>  averaged over its index symmetries, so that
+ * dE/dt = g1 and dE/dv = g2 / 2.  Computed by reverse mode through the sigma
+ * terms, every blocking step and every renormalisation of the left and right
+ * block chains (the forward operators are those the handle holds; the adjoint
+ * keeps one block's and one enlarged block's adjoints at a time and cuts its
+ * sigma-term intermediates under mem_cap_bytes).  FP64 throughout.  Waits for
+ * the result. */
 dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi_dev, const double* lam_dev,
                                 double* g1_dev, double* g2_dev);
+
+/* Replace the integrals (host, caller's numbering, as in dmrg_problem) and drop
+ * every block operator built from the old ones; the loaded or swept MPS basis
+ * and the swept wave function are kept, so that dmrg_prepare / dmrg_expectation
+ * / dmrg_sigma_backward then evaluate the new Hamiltonian in the same basis
+ * (how a caller differentiates E(t, v) at a fixed state, e.g. through
+ * torch.autograd or by finite differences). */
+dmrg_status dmrg_set_integrals(dmrg_handle* h, const double* t, const double* v);
+
+/* The wave function the last dmrg_sweep left (at the bond it stopped on, in
+ * that bond's dmrg_layout): *bond, *psi_size, and a device copy into psi_dev
+ * (may be NULL to query the size). */
+dmrg_status dmrg_sweep_state(dmrg_handle* h, int32_t* bond, int64_t* psi_size, double* psi_dev);
+
+/* <lam| H_eff |psi> at `bond` with the FP64 sigma (device vectors; *value on
+ * the host). */
+dmrg_status dmrg_expectation(dmrg_handle* h, int32_t bond, const double* lam_dev, const double* psi_dev,
+                             double* value);
+
+/* Orbital gradient (Sec. 2.2: orbital rotations U = exp(kappa), kappa real
+ * antisymmetric, rotating t -> U t U^T and every index of v alike): with the
+ * generalised Fock matrix F_pq = sum_r t_pr g1_qr + sum_rst v_prst g2_qrst of
+ * the handle's current integrals and the density matrices g1, g2 (device, as
+ * dmrg_sigma_backward writes them), grad[p*L + q] = dE/dkappa_pq at kappa = 0
+ * = 2 (F_qp - F_pq) (device, L^2 doubles, antisymmetric). */
+dmrg_status dmrg_orbital_gradient(dmrg_handle* h, const double* g1_dev, const double* g2_dev, double* grad_dev);
 
 /* Statistics of the prepared bond: int64[16] = psi_size, n_terms,
  * flops_stage1, flops_stage2 (algorithmic sigma flops), operator_bytes,

@@ -18,7 +18,8 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOCONV, ERR_NONFINITE, ERR_STAT
 PREC_FP64, PREC_MIXED_BF16 = 0, 1
 
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
-           "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_ex", "dmrg_sweep_log", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_stats",
+           "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_ex", "dmrg_sweep_log", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_set_integrals",
+           "dmrg_sweep_state", "dmrg_expectation", "dmrg_orbital_gradient", "dmrg_stats",
            "dmrg_plan_paths", "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
            "dmrg_last_error"]
 SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
@@ -65,6 +66,10 @@ def load_library(path: str | None = None):
         "dmrg_sweep_log": ([vp, ip, ctypes.POINTER(dp), ip, ctypes.POINTER(ip)], ctypes.c_int),
         "dmrg_sweep_phases": ([vp, dp], ctypes.c_int),
         "dmrg_sigma_backward": ([vp, i32, vp, vp, vp, vp], ctypes.c_int),
+        "dmrg_set_integrals": ([vp, dp, dp], ctypes.c_int),
+        "dmrg_sweep_state": ([vp, ip, i64p, vp], ctypes.c_int),
+        "dmrg_expectation": ([vp, i32, vp, vp, dp], ctypes.c_int),
+        "dmrg_orbital_gradient": ([vp, vp, vp, vp], ctypes.c_int),
         "dmrg_stats": ([vp, i64p], ctypes.c_int),
         "dmrg_plan_paths": ([vp, i64p], ctypes.c_int),
         "dmrg_profile": ([vp, i32, dp], ctypes.c_int),
@@ -218,6 +223,30 @@ class Dmrg:
         self._check(self.lib.dmrg_sigma_backward(self.h, bond, ctypes.c_void_p(int(psi_ptr)),
                                                  ctypes.c_void_p(int(lam_ptr)), ctypes.c_void_p(int(g1_ptr)),
                                                  ctypes.c_void_p(int(g2_ptr))))
+
+    def set_integrals(self, t, v):
+        """New integrals (caller's numbering) for the same MPS basis; block operators are rebuilt on demand."""
+        self.t = np.ascontiguousarray(t, dtype=np.float64)
+        self.v = np.ascontiguousarray(v, dtype=np.float64)
+        self._check(self.lib.dmrg_set_integrals(self.h, _dp(self.t), _dp(self.v)))
+
+    def sweep_state(self, psi_ptr=None):
+        """(bond, psi_size) of the state the last sweep left; copies it to psi_ptr if given."""
+        b = ctypes.c_int32()
+        n = ctypes.c_int64()
+        self._check(self.lib.dmrg_sweep_state(self.h, ctypes.byref(b), ctypes.byref(n),
+                                              ctypes.c_void_p(int(psi_ptr)) if psi_ptr else None))
+        return b.value, n.value
+
+    def expectation(self, bond, lam_ptr, psi_ptr):
+        out = ctypes.c_double()
+        self._check(self.lib.dmrg_expectation(self.h, bond, ctypes.c_void_p(int(lam_ptr)),
+                                              ctypes.c_void_p(int(psi_ptr)), ctypes.byref(out)))
+        return out.value
+
+    def orbital_gradient(self, g1_ptr, g2_ptr, grad_ptr):
+        self._check(self.lib.dmrg_orbital_gradient(self.h, ctypes.c_void_p(int(g1_ptr)), ctypes.c_void_p(int(g2_ptr)),
+                                                   ctypes.c_void_p(int(grad_ptr))))
 
     def profile_start(self):
         self._check(self.lib.dmrg_profile(self.h, 1, None))

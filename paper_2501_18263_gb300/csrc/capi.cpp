@@ -29,6 +29,21 @@ bool finite(const double* p, size_t n) {
 
 dmrg_status check_device(dmrg_handle* h) { return dmrg_internal_check_device(h); }
 
+// integrals in the caller's numbering -> chain order (position i holds orbital ord[i])
+void to_chain(int L, const std::vector<int>& ord, const double* t, const double* v, std::vector<double>& tc,
+              std::vector<double>& vc) {
+  const size_t L2 = size_t(L) * L;
+  tc.resize(L2);
+  vc.resize(L2 * L2);
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j) tc[size_t(i) * L + j] = t[size_t(ord[i]) * L + ord[j]];
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j)
+      for (int k = 0; k < L; ++k)
+        for (int l = 0; l < L; ++l)
+          vc[((size_t(i) * L + j) * L + k) * L + l] = v[((size_t(ord[i]) * L + ord[j]) * L + ord[k]) * L + ord[l]];
+}
+
 dmrg_status ensure_bond(dmrg_handle* h, int bond) {
   if (bond < 0 || bond > h->L - 2) return fail(DMRG_ERR_ARG, "bond out of range");
   if (h->eng->bond() != bond) {
@@ -72,18 +87,12 @@ dmrg_status dmrg_build_ops(const dmrg_problem* p, void* stream, dmrg_handle** ou
     P.seed = p->seed;
     P.precision = p->precision;
     P.mem_cap = p->mem_cap_bytes;
-    P.t.resize(L2);
-    P.v.resize(L4);
-    for (int i = 0; i < L; ++i)
-      for (int j = 0; j < L; ++j) P.t[size_t(i) * L + j] = p->t[size_t(ord[i]) * L + ord[j]];
-    for (int i = 0; i < L; ++i)
-      for (int j = 0; j < L; ++j)
-        for (int k = 0; k < L; ++k)
-          for (int l = 0; l < L; ++l)
-            P.v[((size_t(i) * L + j) * L + k) * L + l] =
-                p->v[((size_t(ord[i]) * L + ord[j]) * L + ord[k]) * L + ord[l]];
+    P.ord = ord;
+    to_chain(L, ord, p->t, p->v, P.t, P.v);
     auto h = std::make_unique<dmrg_handle>();
     h->L = L;
+    h->t_user.assign(p->t, p->t + L2);
+    h->v_user.assign(p->v, p->v + L4);
     cudaGetDevice(&h->device);
     h->right_loaded = L;
     h->ex.reset(dmrg::make_cuda_exec(stream, p->precision));
@@ -301,8 +310,102 @@ dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi,
                                 double* g1, double* g2) {
   return guard([&]() -> dmrg_status {
     if (!h || !psi || !lam || !g1 || !g2) return fail(DMRG_ERR_ARG, "null argument");
-    if (bond < 0 || bond > h->L - 2) return fail(DMRG_ERR_ARG, "bond out of range");
-    h->eng->rdm(lam, psi, g1, g2);   // not built: reports it
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    const int L = h->L;
+    const size_t L2 = size_t(L) * L, L4 = L2 * L2;
+    std::vector<double> raw;
+    h->eng->integral_gradient(lam, psi, raw);
+    s = check_device(h);
+    if (s != DMRG_OK) return s;
+    // symmetric parts in the caller's numbering: g1 = sym2(dF/dt), g2 = 2 sym8(dF/dv)
+    const std::vector<int>& o = h->eng->problem().ord;
+    std::vector<double> a1(L2), a2(L4);
+    dmrg::Exec* ex = h->eng->exec();
+    ex->d2h(a1.data(), g1, L2 * sizeof(double));
+    ex->d2h(a2.data(), g2, L4 * sizeof(double));
+    auto T = [&](int i, int j) { return raw[size_t(i) * L + j]; };
+    auto V = [&](int i, int j, int k, int l) { return raw[L2 + ((size_t(i) * L + j) * L + k) * L + l]; };
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j < L; ++j) a1[size_t(o[i]) * L + o[j]] += 0.5 * (T(i, j) + T(j, i));
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j < L; ++j)
+        for (int k = 0; k < L; ++k)
+          for (int l = 0; l < L; ++l) {
+            const double x = V(i, j, k, l) + V(j, i, k, l) + V(i, j, l, k) + V(j, i, l, k) + V(k, l, i, j) +
+                             V(l, k, i, j) + V(k, l, j, i) + V(l, k, j, i);
+            a2[((size_t(o[i]) * L + o[j]) * L + o[k]) * L + o[l]] += 0.25 * x;
+          }
+    for (double x : raw)
+      if (!std::isfinite(x)) return fail(DMRG_ERR_NONFINITE, "non-finite derivative");
+    ex->h2d(g1, a1.data(), L2 * sizeof(double));
+    ex->h2d(g2, a2.data(), L4 * sizeof(double));
+    ex->sync();
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_set_integrals(dmrg_handle* h, const double* t, const double* v) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !t || !v) return fail(DMRG_ERR_ARG, "null argument");
+    const int L = h->L;
+    const size_t L2 = size_t(L) * L, L4 = L2 * L2;
+    if (!finite(t, L2) || !finite(v, L4)) return fail(DMRG_ERR_NONFINITE, "non-finite integrals");
+    std::vector<double> tc, vc;
+    to_chain(L, h->eng->problem().ord, t, v, tc, vc);
+    h->eng->set_integrals(tc, vc);
+    h->t_user.assign(t, t + L2);
+    h->v_user.assign(v, v + L4);
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_sweep_state(dmrg_handle* h, int32_t* bond, int64_t* psi_size, double* psi_dev) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !bond || !psi_size) return fail(DMRG_ERR_ARG, "null argument");
+    const double* p = h->eng->sweep_psi();
+    if (!p || h->eng->bond() < 0) return fail(DMRG_ERR_ARG, "no swept state (call dmrg_sweep first)");
+    *bond = h->eng->bond();
+    *psi_size = h->eng->psi_size();
+    if (psi_dev) {
+      h->eng->exec()->d2d(psi_dev, p, size_t(h->eng->psi_size()) * sizeof(double));
+      h->eng->exec()->sync();
+    }
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_expectation(dmrg_handle* h, int32_t bond, const double* lam, const double* psi, double* value) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !lam || !psi || !value) return fail(DMRG_ERR_ARG, "null argument");
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    dmrg::Exec* ex = h->ex.get();
+    const int64_t n = h->eng->psi_size();
+    double* d = static_cast<double*>(ex->alloc(size_t(n + 1) * sizeof(double)));
+    h->eng->sigma(psi, d);
+    ex->mdot(lam, n, 1, d, n, 1, n, d + n, 1);
+    ex->d2h(value, d + n, sizeof(double));
+    ex->release(d);
+    s = check_device(h);
+    if (s != DMRG_OK) return s;
+    if (!std::isfinite(*value)) return fail(DMRG_ERR_NONFINITE, "non-finite expectation value");
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_orbital_gradient(dmrg_handle* h, const double* g1, const double* g2, double* grad) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !g1 || !g2 || !grad) return fail(DMRG_ERR_ARG, "null argument");
+    dmrg::Exec* ex = h->ex.get();
+    const int L = h->L;
+    const size_t L2 = size_t(L) * L, L4 = L2 * L2;
+    double* d = static_cast<double*>(ex->alloc((L2 + L4) * sizeof(double)));
+    ex->h2d(d, h->t_user.data(), L2 * sizeof(double));
+    ex->h2d(d + L2, h->v_user.data(), L4 * sizeof(double));
+    ex->orbital_gradient(L, d, d + L2, g1, g2, grad);
+    ex->sync();
+    ex->release(d);
     return DMRG_OK;
   });
 }

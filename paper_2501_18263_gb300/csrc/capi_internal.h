@@ -21,6 +21,7 @@ struct dmrg_handle {
   int right_loaded = -1;   // lowest right site loaded (L if none)
   bool any_loaded = false;
   std::vector<dmrg_batch*> batches;   // live batches that use this handle
+  std::vector<double> t_user, v_user; // integrals in the caller's orbital numbering
   std::vector<double> log_rows;       // dmrg_sweep_log tables (library-owned)
   std::vector<int32_t> log_kept;
 };

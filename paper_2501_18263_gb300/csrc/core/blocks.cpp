@@ -90,14 +90,69 @@ double Problem::g(int p, int q, int r, int s) const {
 }
 
 // ---------------------------------------------------------------------------
+// coefficients: numbers (the forward blocking) or linear forms in the integrals
+// (the same blocking recorded for the adjoint)
+
+namespace {
+
+inline bool nz(double x) { return x != 0.0; }
+inline bool nz(const Lin& x) { return x.c0 != 0.0 || !x.w.empty(); }
+inline Lin operator*(Lin a, double s) {
+  a.c0 *= s;
+  for (auto& p : a.w) p.second *= s;
+  return a;
+}
+inline Lin operator*(double s, const Lin& a) { return a * s; }
+inline Lin operator+(Lin a, const Lin& b) {
+  a.c0 += b.c0;
+  a.w.insert(a.w.end(), b.w.begin(), b.w.end());
+  return a;
+}
+inline Lin operator-(const Lin& a, const Lin& b) { return a + b * -1.0; }
+// every blocking coefficient is a constant times a linear form: never a product of two
+inline Lin operator*(const Lin& a, const Lin& b) {
+  if (a.w.empty()) return b * a.c0;
+  if (b.w.empty()) return a * b.c0;
+  throw std::runtime_error("blocking coefficient is not linear in the integrals");
+}
+
+// integral access in the coefficient type
+template <class N>
+struct Ints;
+template <>
+struct Ints<double> {
+  const Problem& P;
+  double h(int p, int q) const { return P.h(p, q); }
+  double g(int p, int q, int r, int s) const { return P.g(p, q, r, s); }
+};
+template <>
+struct Ints<Lin> {
+  const Problem& P;
+  Lin h(int p, int q) const {
+    if ((p & 1) != (q & 1)) return Lin{};
+    return Lin{0.0, {{int64_t(p >> 1) * P.L + (q >> 1), 1.0}}};
+  }
+  Lin g(int p, int q, int r, int s) const {
+    if ((p & 1) != (q & 1) || (r & 1) != (s & 1)) return Lin{};
+    const int64_t L = P.L, i = p >> 1, j = q >> 1, k = r >> 1, l = s >> 1;
+    return Lin{0.0, {{L * L + ((i * L + j) * L + k) * L + l, 1.0}}};
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // one-orbital matrices (basis 0, beta, alpha, alpha beta)
 
-bool Site4::zero() const {
+template <class N>
+bool Site4T<N>::zero() const {
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j)
-      if (m[i][j] != 0.0) return false;
+      if (nz(m[i][j])) return false;
   return true;
 }
+template struct Site4T<double>;
+template struct Site4T<Lin>;
 
 Site4 site_cdag(int sigma) {
   Site4 x;
@@ -148,12 +203,45 @@ static Site4 site_id() {
 
 namespace {
 
+// x + c y for a constant matrix y (entries of y that are zero add nothing)
+template <class N>
+Site4T<N> axpy(const Site4T<N>& a, const N& c, const Site4& b) {
+  Site4T<N> x = a;
+  if (a.zero()) x.odd = b.odd;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      if (b.m[i][j] != 0.0) x.m[i][j] = x.m[i][j] + c * b.m[i][j];
+  return x;
+}
+template <class N>
+Site4T<N> transpose(const Site4T<N>& a) {
+  Site4T<N> x;
+  x.odd = a.odd;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) x.m[i][j] = a.m[j][i];
+  return x;
+}
+template <class N>
+Site4T<N> lift(const Site4& a);
+template <>
+Site4 lift<double>(const Site4& a) { return a; }
+template <>
+Site4T<Lin> lift<Lin>(const Site4& a) {
+  Site4T<Lin> x;
+  x.odd = a.odd;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      if (a.m[i][j] != 0.0) x.m[i][j] = Lin{a.m[i][j], {}};
+  return x;
+}
+
+template <class N>
 struct SiteOps {
-  const Problem& P;
+  Ints<N> I;
   int site;
   int X[2];
   Site4 cd[2], c[2];
-  SiteOps(const Problem& p, int s) : P(p), site(s) {
+  SiteOps(const Problem& p, int s) : I{p}, site(s) {
     X[0] = 2 * s;
     X[1] = 2 * s + 1;
     for (int k = 0; k < 2; ++k) {
@@ -166,63 +254,67 @@ struct SiteOps {
   Site4 prod(const Site4& a, const Site4& b) const { return site_mul(a, b); }
   Site4 prod(const Site4& a, const Site4& b, const Site4& d) const { return site_mul(site_mul(a, b), d); }
   // H restricted to the orbital
-  Site4 H() const {
-    Site4 r;
+  Site4T<N> H() const {
+    Site4T<N> r;
     for (int p : X)
-      for (int q : X)
-        if (P.h(p, q) != 0) r = site_axpy(r, P.h(p, q), prod(CD(p), CC(q)));
+      for (int q : X) {
+        const N h = I.h(p, q);
+        if (nz(h)) r = axpy(r, h, prod(CD(p), CC(q)));
+      }
     for (int p : X)
       for (int q : X)
         for (int rr : X)
           for (int s : X) {
-            double g = P.g(p, q, rr, s);
-            if (g != 0) r = site_axpy(r, 0.5 * g, site_mul(prod(CD(p), CD(rr), CC(s)), CC(q)));
+            const N g = I.g(p, q, rr, s);
+            if (nz(g)) r = axpy(r, g * 0.5, site_mul(prod(CD(p), CD(rr), CC(s)), CC(q)));
           }
     return r;
   }
   // T_p restricted to the orbital (p outside): sum_q h_pq a_q + sum_qrs (pq|rs) a+_r a_s a_q
-  Site4 T(int p) const {
-    Site4 r;
+  Site4T<N> T(int p) const {
+    Site4T<N> r;
     r.odd = 1;
-    for (int q : X)
-      if (P.h(p, q) != 0) r = site_axpy(r, P.h(p, q), CC(q));
+    for (int q : X) {
+      const N h = I.h(p, q);
+      if (nz(h)) r = axpy(r, h, CC(q));
+    }
     for (int q : X)
       for (int rr : X)
         for (int s : X) {
-          double g = P.g(p, q, rr, s);
-          if (g != 0) r = site_axpy(r, g, prod(CD(rr), CC(s), CC(q)));
+          const N g = I.g(p, q, rr, s);
+          if (nz(g)) r = axpy(r, g, prod(CD(rr), CC(s), CC(q)));
         }
     return r;
   }
   // S_q restricted to the orbital (q outside): sum_prs (pq|rs) a+_p a+_r a_s
-  Site4 S(int q) const {
-    Site4 r;
+  Site4T<N> S(int q) const {
+    Site4T<N> r;
     r.odd = 1;
     for (int p : X)
       for (int rr : X)
         for (int s : X) {
-          double g = P.g(p, q, rr, s);
-          if (g != 0) r = site_axpy(r, g, prod(CD(p), CD(rr), CC(s)));
+          const N g = I.g(p, q, rr, s);
+          if (nz(g)) r = axpy(r, g, prod(CD(p), CD(rr), CC(s)));
         }
     return r;
   }
   // P_pr restricted: sum_qs (pq|rs) a_s a_q
-  Site4 Pc(int p, int rr) const {
-    Site4 r;
+  Site4T<N> Pc(int p, int rr) const {
+    Site4T<N> r;
     for (int q : X)
       for (int s : X) {
-        double g = P.g(p, q, rr, s);
-        if (g != 0) r = site_axpy(r, g, prod(CC(s), CC(q)));
+        const N g = I.g(p, q, rr, s);
+        if (nz(g)) r = axpy(r, g, prod(CC(s), CC(q)));
       }
     return r;
   }
   // Q_pq restricted: sum_rs ((pq|rs) - (ps|rq)) a+_r a_s
-  Site4 Qc(int p, int q) const {
-    Site4 r;
+  Site4T<N> Qc(int p, int q) const {
+    Site4T<N> r;
     for (int rr : X)
       for (int s : X) {
-        double g = P.g(p, q, rr, s) - P.g(p, s, rr, q);
-        if (g != 0) r = site_axpy(r, g, prod(CD(rr), CC(s)));
+        const N g = I.g(p, q, rr, s) - I.g(p, s, rr, q);
+        if (nz(g)) r = axpy(r, g, prod(CD(rr), CC(s)));
       }
     return r;
   }
@@ -312,19 +404,22 @@ void Engine::alloc_opset(OpSet& s) {
 
 namespace {
 
+template <class N>
 struct Pend {
   const Op* src;      // nullptr: identity on the block
   const OpSet* set;
   int blk;            // block index in src (-1 for identity)
   int trans;
-  double coef;
+  N coef;
 };
 
+template <class N>
 struct EnlOpBuild {
   Op op;
-  std::map<std::pair<int, int>, std::vector<Pend>> tgt;
+  std::map<std::pair<int, int>, std::vector<Pend<N>>> tgt;
 };
 
+template <class N>
 struct Blocker {
   const Enlarged& E;
   const Sectors& part;
@@ -334,21 +429,21 @@ struct Blocker {
 
   // target += coef * (op or identity, maybe transposed) (x) M   [left: block (x) site]
   //        += coef * M (x) (op ...)                              [right: site (x) block]
-  void add(EnlOpBuild& t, const Op* op, int trans, const Site4& M, double coef) {
-    if (coef == 0.0 || M.zero()) return;
+  void add(EnlOpBuild<N>& t, const Op* op, int trans, const Site4T<N>& M, const N& coef) {
+    if (!nz(coef) || M.zero()) return;
     if (op && op->blk.empty()) return;
     int src_odd = op ? op->odd : 0;
     for (int s2 = 0; s2 < 4; ++s2)
       for (int s = 0; s < 4; ++s) {
-        double mv = M.m[s2][s];
-        if (mv == 0.0) continue;
+        const N& mv = M.m[s2][s];
+        if (!nz(mv)) continue;
         int nsite = kLocalQ[s].n();
         if (!op) {
           for (size_t k = 0; k < part.q.size(); ++k) {
             int rf = E.part_s_to_fine[k][s2], cf = E.part_s_to_fine[k][s];
             double sg = 1.0;
             if (left && M.odd && (part.q[k].n() & 1)) sg = -1.0;
-            t.tgt[{rf, cf}].push_back(Pend{nullptr, &src, -1, 0, coef * mv * sg});
+            t.tgt[{rf, cf}].push_back(Pend<N>{nullptr, &src, -1, 0, coef * mv * sg});
           }
         } else {
           for (size_t bi = 0; bi < op->blk.size(); ++bi) {
@@ -361,118 +456,132 @@ struct Blocker {
             } else {
               if (src_odd && (nsite & 1)) sg = -1.0;
             }
-            t.tgt[{rf, cf}].push_back(Pend{op, &src, int(bi), trans, coef * mv * sg});
+            t.tgt[{rf, cf}].push_back(Pend<N>{op, &src, int(bi), trans, coef * mv * sg});
           }
         }
       }
   }
 };
 
-}  // namespace
+template <class N>
+N num(double x);
+template <>
+double num<double>(double x) { return x; }
+template <>
+Lin num<Lin>(double x) { return Lin{x, {}}; }
 
-void Engine::enlarge(bool left, const Block& blk, int site, Enlarged& E, OpSet& out) {
+// The blocking step (block (x) site for a left block, site (x) block for a right
+// one): every fine block of every operator of the enlarged block as a list of
+// contributions coef * (block operator block, or the identity) (x) site matrix
+// entry.  N = double gives the numbers; N = Lin the same list with every
+// coefficient kept as a linear form in the integrals.
+template <class N>
+std::map<OpKey, EnlOpBuild<N>> collect_blocking(const Problem& P, bool left, const Block& blk, int site,
+                                                Enlarged& E) {
   E.build(blk.sec, left);
-  const int L = P_.L;
-  SiteOps so(P_, site);
+  const int L = P.L;
+  SiteOps<N> so(P, site);
+  const Ints<N>& I = so.I;
   const int X0 = 2 * site, X1 = 2 * site + 1;
   const int X[2] = {X0, X1};
-  Site4 I4 = site_id();
-  Blocker bl(E, blk.sec, blk.ops);
+  const Site4 I4 = site_id();
+  const N one = num<N>(1.0), mone = num<N>(-1.0);
+  Blocker<N> bl(E, blk.sec, blk.ops);
   static const Op kEmpty;  // absent operator = zero (never the identity)
   auto G = [&](int t, int i, int j = 0) -> const Op* {
     const Op* o = blk.ops.get(t, i, j);
     return o ? o : &kEmpty;
   };
   // B_ps for any order (transposed storage for p > s)
-  auto addB = [&](EnlOpBuild& t, int p, int s, const Site4& M, double c) {
+  auto addB = [&](EnlOpBuild<N>& t, int p, int s, const Site4T<N>& M, const N& c) {
     if (p <= s) bl.add(t, G(OP_B, p, s), 0, M, c);
     else bl.add(t, G(OP_B, s, p), 1, M, c);
   };
 
-  std::map<OpKey, EnlOpBuild> build;
+  std::map<OpKey, EnlOpBuild<N>> build;
   std::vector<OpKey> keys = left ? left_keys(site + 1, L) : right_keys(site, L);
   for (const OpKey& k : keys) {
-    EnlOpBuild& t = build[k];
+    EnlOpBuild<N>& t = build[k];
     key_qn(k, t.op.delta, t.op.odd);
   }
 
   if (left) {
     const int nB = 2 * site;  // block spin-orbitals [0, nB)
     for (const OpKey& k : keys) {
-      EnlOpBuild& t = build[k];
+      EnlOpBuild<N>& t = build[k];
       switch (k.type) {
         case OP_H: {
-          bl.add(t, G(OP_H, 0), 0, I4, 1.0);
-          bl.add(t, nullptr, 0, so.H(), 1.0);
+          bl.add(t, G(OP_H, 0), 0, lift<N>(I4), one);
+          bl.add(t, nullptr, 0, so.H(), one);
           for (int p = 0; p < nB; ++p) {
-            Site4 Tp = so.T(p);
-            bl.add(t, G(OP_C, p), 0, Tp, 1.0);
-            bl.add(t, G(OP_C, p), 1, site_T(Tp), -1.0);
+            Site4T<N> Tp = so.T(p);
+            bl.add(t, G(OP_C, p), 0, Tp, one);
+            bl.add(t, G(OP_C, p), 1, transpose(Tp), mone);
           }
           for (int q : X) {
-            bl.add(t, G(OP_S, q), 0, so.CC(q), 1.0);
-            bl.add(t, G(OP_S, q), 1, so.CD(q), -1.0);
+            bl.add(t, G(OP_S, q), 0, lift<N>(so.CC(q)), one);
+            bl.add(t, G(OP_S, q), 1, lift<N>(so.CD(q)), mone);
           }
           for (int p = 0; p < nB; ++p)
             for (int r = p + 1; r < nB; ++r) {
-              Site4 Pm = so.Pc(p, r);
-              bl.add(t, G(OP_A, p, r), 0, Pm, 1.0);
-              bl.add(t, G(OP_A, p, r), 1, site_T(Pm), 1.0);
+              Site4T<N> Pm = so.Pc(p, r);
+              bl.add(t, G(OP_A, p, r), 0, Pm, one);
+              bl.add(t, G(OP_A, p, r), 1, transpose(Pm), one);
             }
           for (int p = 0; p < nB; ++p)
             for (int q = p; q < nB; ++q) {
-              Site4 Qm = so.Qc(p, q);
-              bl.add(t, G(OP_B, p, q), 0, Qm, 1.0);
-              if (p < q) bl.add(t, G(OP_B, p, q), 1, site_T(Qm), 1.0);
+              Site4T<N> Qm = so.Qc(p, q);
+              bl.add(t, G(OP_B, p, q), 0, Qm, one);
+              if (p < q) bl.add(t, G(OP_B, p, q), 1, transpose(Qm), one);
             }
           break;
         }
         case OP_C:
-          if (k.i < nB) bl.add(t, G(OP_C, k.i), 0, I4, 1.0);
-          else bl.add(t, nullptr, 0, so.CD(k.i), 1.0);
+          if (k.i < nB) bl.add(t, G(OP_C, k.i), 0, lift<N>(I4), one);
+          else bl.add(t, nullptr, 0, lift<N>(so.CD(k.i)), one);
           break;
         case OP_A:
-          if (k.j < nB) bl.add(t, G(OP_A, k.i, k.j), 0, I4, 1.0);
-          else if (k.i < nB) bl.add(t, G(OP_C, k.i), 0, so.CD(k.j), 1.0);
-          else bl.add(t, nullptr, 0, so.prod(so.CD(k.i), so.CD(k.j)), 1.0);
+          if (k.j < nB) bl.add(t, G(OP_A, k.i, k.j), 0, lift<N>(I4), one);
+          else if (k.i < nB) bl.add(t, G(OP_C, k.i), 0, lift<N>(so.CD(k.j)), one);
+          else bl.add(t, nullptr, 0, lift<N>(so.prod(so.CD(k.i), so.CD(k.j))), one);
           break;
         case OP_B:
-          if (k.j < nB) bl.add(t, G(OP_B, k.i, k.j), 0, I4, 1.0);
-          else if (k.i < nB) bl.add(t, G(OP_C, k.i), 0, so.CC(k.j), 1.0);
-          else bl.add(t, nullptr, 0, so.prod(so.CD(k.i), so.CC(k.j)), 1.0);
+          if (k.j < nB) bl.add(t, G(OP_B, k.i, k.j), 0, lift<N>(I4), one);
+          else if (k.i < nB) bl.add(t, G(OP_C, k.i), 0, lift<N>(so.CC(k.j)), one);
+          else bl.add(t, nullptr, 0, lift<N>(so.prod(so.CD(k.i), so.CC(k.j))), one);
           break;
         case OP_S: {
           const int q = k.i;
-          bl.add(t, G(OP_S, q), 0, I4, 1.0);
-          bl.add(t, nullptr, 0, so.S(q), 1.0);
+          bl.add(t, G(OP_S, q), 0, lift<N>(I4), one);
+          bl.add(t, nullptr, 0, so.S(q), one);
           // two block operators, one site operator
           for (int s : X)
             for (int p = 0; p < nB; ++p)
               for (int r = p + 1; r < nB; ++r) {
-                double c = P_.g(p, q, r, s) - P_.g(r, q, p, s);
-                if (c != 0.0) bl.add(t, G(OP_A, p, r), 0, so.CC(s), c);
+                const N c = I.g(p, q, r, s) - I.g(r, q, p, s);
+                if (nz(c)) bl.add(t, G(OP_A, p, r), 0, lift<N>(so.CC(s)), c);
               }
           for (int x : X)
             for (int p = 0; p < nB; ++p)
               for (int s = 0; s < nB; ++s) {
-                double c = P_.g(x, q, p, s) - P_.g(p, q, x, s);
-                if (c != 0.0) addB(t, p, s, so.CD(x), c);
+                const N c = I.g(x, q, p, s) - I.g(p, q, x, s);
+                if (nz(c)) addB(t, p, s, lift<N>(so.CD(x)), c);
               }
           // one block operator, two site operators
           for (int y = 0; y < nB; ++y) {
-            Site4 M1, M2;
+            Site4T<N> M1, M2;
             for (int r : X)
               for (int s : X) {
-                double c = P_.g(y, q, r, s) - P_.g(r, q, y, s);
-                if (c != 0.0) M1 = site_axpy(M1, c, so.prod(so.CD(r), so.CC(s)));
+                const N c = I.g(y, q, r, s) - I.g(r, q, y, s);
+                if (nz(c)) M1 = axpy(M1, c, so.prod(so.CD(r), so.CC(s)));
               }
             for (int p : X)
               for (int r : X) {
-                double c = P_.g(p, q, r, y);
-                if (c != 0.0) M2 = site_axpy(M2, c, so.prod(so.CD(p), so.CD(r)));
+                const N c = I.g(p, q, r, y);
+                if (nz(c)) M2 = axpy(M2, c, so.prod(so.CD(p), so.CD(r)));
               }
-            bl.add(t, G(OP_C, y), 0, M1, 1.0);
-            bl.add(t, G(OP_C, y), 1, M2, 1.0);
+            bl.add(t, G(OP_C, y), 0, M1, one);
+            bl.add(t, G(OP_C, y), 1, M2, one);
           }
           break;
         }
@@ -483,84 +592,84 @@ void Engine::enlarge(bool left, const Block& blk, int site, Enlarged& E, OpSet& 
   } else {
     const int c0 = 2 * (site + 1);  // block spin-orbitals [c0, 2L)
     for (const OpKey& k : keys) {
-      EnlOpBuild& t = build[k];
+      EnlOpBuild<N>& t = build[k];
       switch (k.type) {
         case OP_H: {
-          bl.add(t, G(OP_H, 0), 0, I4, 1.0);
-          bl.add(t, nullptr, 0, so.H(), 1.0);
+          bl.add(t, G(OP_H, 0), 0, lift<N>(I4), one);
+          bl.add(t, nullptr, 0, so.H(), one);
           for (int p : X) {
-            bl.add(t, G(OP_T, p), 0, so.CD(p), 1.0);
-            bl.add(t, G(OP_T, p), 1, so.CC(p), -1.0);
+            bl.add(t, G(OP_T, p), 0, lift<N>(so.CD(p)), one);
+            bl.add(t, G(OP_T, p), 1, lift<N>(so.CC(p)), mone);
           }
           for (int q = c0; q < 2 * L; ++q) {
-            Site4 Sq = so.S(q);
-            bl.add(t, G(OP_C, q), 1, Sq, 1.0);
-            bl.add(t, G(OP_C, q), 0, site_T(Sq), -1.0);
+            Site4T<N> Sq = so.S(q);
+            bl.add(t, G(OP_C, q), 1, Sq, one);
+            bl.add(t, G(OP_C, q), 0, transpose(Sq), mone);
           }
           {
             Site4 A = so.prod(so.CD(X0), so.CD(X1));
-            bl.add(t, G(OP_P, X0, X1), 0, A, 1.0);
-            bl.add(t, G(OP_P, X0, X1), 1, site_T(A), 1.0);
+            bl.add(t, G(OP_P, X0, X1), 0, lift<N>(A), one);
+            bl.add(t, G(OP_P, X0, X1), 1, lift<N>(site_T(A)), one);
           }
           for (int p : X)
             for (int q : X) {
               if (q < p) continue;
               Site4 Bm = so.prod(so.CD(p), so.CC(q));
-              bl.add(t, G(OP_Q, p, q), 0, Bm, 1.0);
-              if (p < q) bl.add(t, G(OP_Q, p, q), 1, site_T(Bm), 1.0);
+              bl.add(t, G(OP_Q, p, q), 0, lift<N>(Bm), one);
+              if (p < q) bl.add(t, G(OP_Q, p, q), 1, lift<N>(site_T(Bm)), one);
             }
           break;
         }
         case OP_C:
-          if (k.i >= c0) bl.add(t, G(OP_C, k.i), 0, I4, 1.0);
-          else bl.add(t, nullptr, 0, so.CD(k.i), 1.0);
+          if (k.i >= c0) bl.add(t, G(OP_C, k.i), 0, lift<N>(I4), one);
+          else bl.add(t, nullptr, 0, lift<N>(so.CD(k.i)), one);
           break;
         case OP_T: {
           const int p = k.i;
-          bl.add(t, nullptr, 0, so.T(p), 1.0);
-          bl.add(t, G(OP_T, p), 0, I4, 1.0);
+          bl.add(t, nullptr, 0, so.T(p), one);
+          bl.add(t, G(OP_T, p), 0, lift<N>(I4), one);
           for (int x : X) {
-            bl.add(t, G(OP_Q, p, x), 0, so.CC(x), 1.0);
-            bl.add(t, G(OP_P, p, x), 0, so.CD(x), 1.0);
+            bl.add(t, G(OP_Q, p, x), 0, lift<N>(so.CC(x)), one);
+            bl.add(t, G(OP_P, p, x), 0, lift<N>(so.CD(x)), one);
           }
           for (int y = c0; y < 2 * L; ++y) {
-            Site4 M1, M2;
+            Site4T<N> M1, M2;
             for (int r : X)
               for (int s : X) {
-                double c = P_.g(p, y, r, s) - P_.g(p, s, r, y);
-                if (c != 0.0) M1 = site_axpy(M1, c, so.prod(so.CD(r), so.CC(s)));
+                const N c = I.g(p, y, r, s) - I.g(p, s, r, y);
+                if (nz(c)) M1 = axpy(M1, c, so.prod(so.CD(r), so.CC(s)));
               }
             for (int q : X)
               for (int s : X) {
-                double c = P_.g(p, q, y, s);
-                if (c != 0.0) M2 = site_axpy(M2, c, so.prod(so.CC(s), so.CC(q)));
+                const N c = I.g(p, q, y, s);
+                if (nz(c)) M2 = axpy(M2, c, so.prod(so.CC(s), so.CC(q)));
               }
-            bl.add(t, G(OP_C, y), 1, M1, 1.0);
-            bl.add(t, G(OP_C, y), 0, M2, 1.0);
+            bl.add(t, G(OP_C, y), 1, M1, one);
+            bl.add(t, G(OP_C, y), 0, M2, one);
           }
           break;
         }
         case OP_P: {
           const int p = k.i, r = k.j;
-          bl.add(t, nullptr, 0, so.Pc(p, r), 1.0);
-          bl.add(t, G(OP_P, p, r), 0, I4, 1.0);
+          bl.add(t, nullptr, 0, so.Pc(p, r), one);
+          bl.add(t, G(OP_P, p, r), 0, lift<N>(I4), one);
           for (int x : X)
             for (int y = c0; y < 2 * L; ++y) {
-              double c = P_.g(p, y, r, x) - P_.g(p, x, r, y);
-              if (c != 0.0) bl.add(t, G(OP_C, y), 1, so.CC(x), c);
+              const N c = I.g(p, y, r, x) - I.g(p, x, r, y);
+              if (nz(c)) bl.add(t, G(OP_C, y), 1, lift<N>(so.CC(x)), c);
             }
           break;
         }
         case OP_Q: {
           const int p = k.i, q = k.j;
-          bl.add(t, nullptr, 0, so.Qc(p, q), 1.0);
-          bl.add(t, G(OP_Q, p, q), 0, I4, 1.0);
+          bl.add(t, nullptr, 0, so.Qc(p, q), one);
+          bl.add(t, G(OP_Q, p, q), 0, lift<N>(I4), one);
           for (int x : X)
             for (int y = c0; y < 2 * L; ++y) {
-              double c1 = P_.g(p, q, x, y) - P_.g(p, y, x, q);
-              if (c1 != 0.0) bl.add(t, G(OP_C, y), 1, so.CD(x), c1);
-              double c2 = P_.g(p, q, y, x) - P_.g(p, x, y, q);
-              if (c2 != 0.0) bl.add(t, G(OP_C, y), 0, so.CC(x), -c2);
+              const N c1 = I.g(p, q, x, y) - I.g(p, y, x, q);
+              if (nz(c1)) bl.add(t, G(OP_C, y), 1, lift<N>(so.CD(x)), c1);
+              const N c2 = I.g(p, q, y, x) - I.g(p, x, y, q);
+              if (nz(c2)) bl.add(t, G(OP_C, y), 0, lift<N>(so.CC(x)), c2 * -1.0);
             }
           break;
         }
@@ -570,10 +679,42 @@ void Engine::enlarge(bool left, const Block& blk, int site, Enlarged& E, OpSet& 
     }
   }
 
+  return build;
+}
+
+}  // namespace
+
+std::vector<BlockingTerm> Engine::blocking_terms(bool left, const Block& blk, int site, Enlarged& E) const {
+  std::map<OpKey, EnlOpBuild<Lin>> build = collect_blocking<Lin>(P_, left, blk, site, E);
+  std::vector<BlockingTerm> out;
+  for (auto& kv : build)
+    for (auto& tg : kv.second.tgt)
+      for (auto& pd : tg.second) {
+        BlockingTerm bt{kv.first, tg.first.first, tg.first.second, pd.src, pd.blk, pd.trans, Lin{pd.coef.c0, {}}};
+        // merge repeated integrals, drop zero weights
+        std::map<int64_t, double> w;
+        for (auto& x : pd.coef.w) w[x.first] += x.second;
+        for (auto& x : w)
+          if (x.second != 0.0) bt.coef.w.push_back(x);
+        out.push_back(std::move(bt));
+      }
+  return out;
+}
+
+double Engine::lin_value(const Lin& c) const {
+  const int64_t L2 = int64_t(P_.L) * P_.L;
+  double x = c.c0;
+  for (auto& w : c.w) x += w.second * (w.first < L2 ? P_.t[size_t(w.first)] : P_.v[size_t(w.first - L2)]);
+  return x;
+}
+
+void Engine::enlarge(bool left, const Block& blk, int site, Enlarged& E, OpSet& out) {
+  std::map<OpKey, EnlOpBuild<double>> build = collect_blocking<double>(P_, left, blk, site, E);
+
   // allocate the fine blocks that received contributions, then emit the kron plan
   free_opset(out);
   for (auto& kv : build) {
-    EnlOpBuild& t = kv.second;
+    EnlOpBuild<double>& t = kv.second;
     Op& o = t.op;
     for (auto& tg : t.tgt) {
       OpBlk b;

@@ -86,16 +86,50 @@ struct OpSet {
   }
 };
 
-// 4x4 matrix on one orbital with definite fermion parity
-struct Site4 {
-  double m[4][4] = {};
+// A coefficient that is linear in the integrals, c0 + sum_k w_k x_{idx_k}, with
+// idx = i L + j for t_ij and L^2 + ((i L + j) L + k) L + l for (ij|kl) (chain order).
+struct Lin {
+  double c0 = 0.0;
+  std::vector<std::pair<int64_t, double>> w;
+};
+
+// 4x4 matrix on one orbital with definite fermion parity; entries are numbers
+// (N = double) or linear forms in the integrals (N = Lin)
+template <class N>
+struct Site4T {
+  N m[4][4] = {};
   int odd = 0;
   bool zero() const;
+};
+using Site4 = Site4T<double>;
+
+// One contribution of the blocking step, recorded for the adjoint: fine block
+// (rf, cf) of the enlarged operator `key` receives coef * (block src_blk of the
+// block operator src, transposed if trans; src == nullptr: the identity on the
+// block part) (x) a site-matrix entry, the entry and the Jordan-Wigner sign
+// folded into coef.
+struct BlockingTerm {
+  OpKey key;
+  int rf, cf;
+  const Op* src;
+  int src_blk, trans;
+  Lin coef;
+};
+
+// One term of H_eff at a bond: c * op(L) (x) op(R), op = transpose if Lt / Rt,
+// nullptr = the identity on that side (Eq. Hamilton_act_U1sym)
+struct SigmaTerm {
+  const Op* L;
+  int Lt;
+  const Op* R;
+  int Rt;
+  double c;
 };
 
 struct Problem {
   int L = 0, na = 0, nb = 0;
   std::vector<double> t, v;  // permuted into chain order
+  std::vector<int> ord;      // chain position -> orbital of the caller's numbering
   int D = 0;
   uint64_t seed = 0;
   int precision = 0;
@@ -177,8 +211,20 @@ class Engine {
   const Block& left_block(int n) const { return lb_[n]; }
   const Block& right_block(int m) const { return rb_[m]; }
 
-  // reduced density matrices at the current bond: g1 += <lam|E|psi>, g2 += ...
-  void rdm(const double* lam, const double* psi, double* g1, double* g2);
+  // Derivatives of F = <lam| H_eff(t, v) |psi> at the prepared bond, for the
+  // fixed MPS basis, with respect to the integrals as this engine reads them (chain
+  // order): raw[i L + j] = dF/dt_ij, raw[L^2 + ((i L + j) L + k) L + l] =
+  // dF/dv_ijkl (host vector of L^2 + L^4).  Reverse mode through the sigma terms,
+  // the blocking steps and the renormalisations of both block chains.
+  void integral_gradient(const double* lam, const double* psi, std::vector<double>& raw);
+  // blocking contributions with their coefficients as linear forms (adjoint)
+  std::vector<BlockingTerm> blocking_terms(bool left, const Block& blk, int site, Enlarged& E) const;
+  double lin_value(const Lin& c) const;
+  // replace the integrals (chain order) and drop every block operator built from
+  // the old ones; the loaded / swept isometries are kept
+  void set_integrals(const std::vector<double>& t, const std::vector<double>& v);
+  // wave function of the last sweep (device, at bond(); nullptr before a sweep)
+  const double* sweep_psi() const { return psi_cur_; }
 
   double last_energy = 0.0;
   double last_rnorm = 0.0;
@@ -273,6 +319,9 @@ class Engine {
   void enlarge(bool left, const Block& blk, int site, Enlarged& E, OpSet& out);
   void renormalize(bool left, const Enlarged& E, const OpSet& eops, const Iso& iso, Block& out);
   void build_sigma_plan();
+  std::vector<SigmaTerm> sigma_terms(bool keep_empty = false) const;   // terms of the prepared bond (all but H_L' (x) 1)
+  void sigma_adjoint(const double* lam, const double* psi, const std::map<OpKey, std::map<std::pair<int, int>, int64_t>>& tl,
+                     double* gl, const std::map<OpKey, std::map<std::pair<int, int>, int64_t>>& tr, double* gr);
   void free_bond();
   void truncate_and_move(bool left_to_right, int D, double* trunc_w, std::vector<int>* kept = nullptr);
 };

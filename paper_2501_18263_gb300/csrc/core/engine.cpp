@@ -183,10 +183,14 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
   int it = 0;
   // Mixed precision: iterate with the split-BF16 sigma; when its residual reaches
   // the level that precision can resolve (or stalls), restart from the Ritz vector
-  // with an FP64 sigma of it.  Corrections added afterwards carry only the small
-  // error of their own (small) coefficients, so the residual is then trusted.
+  // x with an FP64 sigma W0 = H x (a refinement).  Right after a refinement the
+  // residual W0 - theta x is exact, and only an exact residual can declare
+  // convergence.  Later corrections V_i get split-BF16 sigmas, but their couplings
+  // to x are taken from the exact pair (<V_i|H x> = <W0|V_i>, H symmetric), so the
+  // corrections carry only the small error of their own small coefficients.
   const bool mixed = (prec != 0 && refine);
   int refines = 0, last_refine = -100;
+  bool exact0 = false;   // V[0], W[0] are an exact FP64 pair
   double best = 1e300;
   int best_it = 0;
   int status = 2;
@@ -225,13 +229,15 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
         }
       }
     } else {
-      if (refines > 0 && rnorm <= tol) {
+      const bool just_refined = (it == last_refine + 1);   // r is the exact residual of x = V[0]
+      if (just_refined && rnorm <= tol) {
         status = 0;
         break;
       }
       const double floor_m = 1e-6 * std::max(1.0, std::fabs(th));
-      const bool stalled = it - best_it >= 8;
-      if ((rnorm <= std::max(tol, floor_m) || stalled) && it - last_refine >= 4 && refines < 8) {
+      const bool stalled = it - best_it >= 6;
+      const bool want = refines == 0 ? (rnorm <= floor_m || stalled) : (rnorm <= tol || stalled);
+      if (want && !just_refined && refines < 24) {
         ++refines;
         last_refine = it;
         best = 1e300;
@@ -244,6 +250,7 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
         ex_->mdot(V, n, 1, W, n, 1, n, Hs, lds);
         m = 1;
         have_prev = false;
+        exact0 = true;
         continue;
       }
     }
@@ -256,6 +263,7 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
       ex_->zero(Hs, size_t(lds) * lds * sizeof(double));
       ex_->d2d(Hs, theta, sizeof(double));
       m = 1;
+      exact0 = false;
       if (have_prev) {
         double* V1 = V + n;
         double* W1 = W + n;
@@ -299,6 +307,7 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
     ex_->d2d(V + int64_t(m) * n, t, n * sizeof(double));
     apply(V + int64_t(m) * n, W + int64_t(m) * n, prec);
     ex_->mdot(V, n, m + 1, W + int64_t(m) * n, n, 1, n, Hs + m, lds);
+    if (exact0 && prec != 0) ex_->mdot(W, n, 1, V + int64_t(m) * n, n, 1, n, Hs + m, lds);
     ++m;
   }
   // normalised Ritz vector out

@@ -27,13 +27,7 @@ namespace dmrg {
 
 namespace {
 
-struct Term {
-  const Op* L;   // nullptr: identity on L'
-  int Lt;
-  const Op* R;   // nullptr: identity on R'
-  int Rt;
-  double c;
-};
+using Term = SigmaTerm;
 
 // fine block lookup (row fine, col fine) -> block
 using FineMap = std::map<std::pair<int, int>, const OpBlk*>;
@@ -121,9 +115,53 @@ void Engine::prepare_bond(int bond) {
   tick(0);
 }
 
+std::vector<SigmaTerm> Engine::sigma_terms(bool keep_empty) const {
+  const int nL = 2 * (bond_ + 1);
+  const int L = P_.L;
+  auto GL = [&](int t, int i, int j = 0) {
+    const Op* o = EopsL_.get(t, i, j);
+    if (!o) throw std::runtime_error("sigma plan: missing L' operator");
+    return o;
+  };
+  auto GR = [&](int t, int i, int j = 0) {
+    const Op* o = EopsR_.get(t, i, j);
+    if (!o) throw std::runtime_error("sigma plan: missing R' operator");
+    return o;
+  };
+
+  std::vector<SigmaTerm> terms;
+  terms.push_back(SigmaTerm{nullptr, 0, GR(OP_H, 0), 0, 1.0});  // 1 (x) H_R'
+  for (int p = 0; p < nL; ++p) {
+    terms.push_back(SigmaTerm{GL(OP_C, p), 0, GR(OP_T, p), 0, 1.0});
+    terms.push_back(SigmaTerm{GL(OP_C, p), 1, GR(OP_T, p), 1, -1.0});
+  }
+  for (int q = nL; q < 2 * L; ++q) {
+    terms.push_back(SigmaTerm{GL(OP_S, q), 0, GR(OP_C, q), 1, 1.0});
+    terms.push_back(SigmaTerm{GL(OP_S, q), 1, GR(OP_C, q), 0, -1.0});
+  }
+  for (int p = 0; p < nL; ++p)
+    for (int r = p + 1; r < nL; ++r) {
+      terms.push_back(SigmaTerm{GL(OP_A, p, r), 0, GR(OP_P, p, r), 0, 1.0});
+      terms.push_back(SigmaTerm{GL(OP_A, p, r), 1, GR(OP_P, p, r), 1, 1.0});
+    }
+  for (int p = 0; p < nL; ++p)
+    for (int q = p; q < nL; ++q) {
+      terms.push_back(SigmaTerm{GL(OP_B, p, q), 0, GR(OP_Q, p, q), 0, 1.0});
+      if (p < q) terms.push_back(SigmaTerm{GL(OP_B, p, q), 1, GR(OP_Q, p, q), 1, 1.0});
+    }
+  // drop terms with an empty side (the adjoint keeps them: an operator can be zero
+  // for the present integrals and still have a derivative)
+  std::vector<SigmaTerm> T;
+  for (auto& t : terms) {
+    if (!keep_empty && ((t.L && t.L->blk.empty()) || (t.R && t.R->blk.empty()))) continue;
+    if (!t.L && !t.R) continue;
+    T.push_back(t);
+  }
+  return T;
+}
+
 void Engine::build_sigma_plan() {
   ++plan_gen_;
-  const int L = P_.L;
   const int b = bond_;
   const int nL = 2 * (b + 1);  // spin-orbitals of L'
   st_ = BondStats();
@@ -141,34 +179,7 @@ void Engine::build_sigma_plan() {
     if (!o) throw std::runtime_error("sigma plan: missing R' operator");
     return o;
   };
-
-  std::vector<Term> terms;
-  terms.push_back(Term{nullptr, 0, GR(OP_H, 0), 0, 1.0});  // 1 (x) H_R'
-  for (int p = 0; p < nL; ++p) {
-    terms.push_back(Term{GL(OP_C, p), 0, GR(OP_T, p), 0, 1.0});
-    terms.push_back(Term{GL(OP_C, p), 1, GR(OP_T, p), 1, -1.0});
-  }
-  for (int q = nL; q < 2 * L; ++q) {
-    terms.push_back(Term{GL(OP_S, q), 0, GR(OP_C, q), 1, 1.0});
-    terms.push_back(Term{GL(OP_S, q), 1, GR(OP_C, q), 0, -1.0});
-  }
-  for (int p = 0; p < nL; ++p)
-    for (int r = p + 1; r < nL; ++r) {
-      terms.push_back(Term{GL(OP_A, p, r), 0, GR(OP_P, p, r), 0, 1.0});
-      terms.push_back(Term{GL(OP_A, p, r), 1, GR(OP_P, p, r), 1, 1.0});
-    }
-  for (int p = 0; p < nL; ++p)
-    for (int q = p; q < nL; ++q) {
-      terms.push_back(Term{GL(OP_B, p, q), 0, GR(OP_Q, p, q), 0, 1.0});
-      if (p < q) terms.push_back(Term{GL(OP_B, p, q), 1, GR(OP_Q, p, q), 1, 1.0});
-    }
-  // drop terms with an empty side
-  std::vector<Term> T;
-  for (auto& t : terms) {
-    if ((t.L && t.L->blk.empty()) || (t.R && t.R->blk.empty())) continue;
-    if (!t.L && !t.R) continue;
-    T.push_back(t);
-  }
+  const std::vector<Term> T = sigma_terms();
   st_.n_terms = int(T.size()) + 1;
 
   const Enlarged& EL = EL_;
@@ -926,14 +937,226 @@ void Engine::batch_epilogue(double* sig) {
   ex_->df_to_f64(shi_, slo_, sig, psi_n_);
 }
 
-void Engine::rdm(const double* lam, const double* psi, double* g1, double* g2) {
-  (void)lam; (void)psi; (void)g1; (void)g2;
-  throw std::runtime_error("dmrg_sigma_backward: not implemented in this version of the library");
-}
-
 void Engine::diagonal(double* d) {
   if (bond_ < 0) throw std::runtime_error("diagonal: no bond prepared");
   ex_->d2d(d, diag_, psi_n_ * sizeof(double));
+}
+
+}  // namespace dmrg
+
+namespace dmrg {
+
+// Adjoint of the sigma terms (first step of integral_gradient, adjoint.cpp): for
+// F = sum_terms sum_blocks < lam{iT, jT}, c s op(O_L){iT <- iL} psi{iL, jR} op(O_R){jT <- jR}^T >
+// the fine blocks of every L' and R' operator listed in tl / tr receive
+//   dF/d op(O_L) = c s lam op(O_R) psi^T  (via Y = c s lam op(O_R)),
+//   dF/d op(O_R) = c s lam^T op(O_L) psi  (via X = c s op(O_L) psi, the stage-1 product),
+// and H_L' (x) 1 gives dF/dH_L' = lam psi^T, 1 (x) H_R' gives dF/dH_R' = lam^T psi.
+// Terms are processed in chunks so that X and Y stay under the memory cap; every
+// adjoint block is one GEMM problem per chunk (segments summed in a fixed order,
+// accumulated over the chunks in stream order).
+void Engine::sigma_adjoint(const double* lam, const double* psi,
+                           const std::map<OpKey, std::map<std::pair<int, int>, int64_t>>& tl, double* gl,
+                           const std::map<OpKey, std::map<std::pair<int, int>, int64_t>>& tr, double* gr) {
+  const Enlarged& EL = EL_;
+  const Enlarged& ER = ER_;
+  std::map<const Op*, OpKey> keyL, keyR;
+  for (auto& kv : EopsL_.ops) keyL[&kv.second] = kv.first;
+  for (auto& kv : EopsR_.ops) keyR[&kv.second] = kv.first;
+  auto lcoarse = [&](const QN& q) { return EL.coarse.find(q); };
+  auto rcoarse = [&](const QN& q) { return ER.coarse.find(q); };
+  auto target = [](const std::map<OpKey, std::map<std::pair<int, int>, int64_t>>& tm, const OpKey& k, int r,
+                   int c) -> int64_t {
+    auto it = tm.find(k);
+    if (it == tm.end()) return -1;
+    auto jt = it->second.find({r, c});
+    return jt == it->second.end() ? -1 : jt->second;
+  };
+  const std::vector<Term> T = sigma_terms(true);
+  struct XB { int iL, jR, iT, jT; int64_t off; };
+  std::vector<std::vector<XB>> xl(T.size());
+  std::vector<int64_t> xsize(T.size(), 0);
+  for (size_t n = 0; n < T.size(); ++n) {
+    const Term& t = T[n];
+    const QN dL = !t.L ? QN{0, 0} : (t.Lt ? QN{0, 0} - t.L->delta : t.L->delta);
+    const QN dR = t.Rt ? QN{0, 0} - t.R->delta : t.R->delta;
+    int64_t o = 0;
+    for (size_t iL = 0; iL < EL.coarse.q.size(); ++iL) {
+      if (psi_off_[iL] < 0) continue;
+      const int jR = psi_rcoarse_[iL];
+      const int iT = lcoarse(EL.coarse.q[iL] + dL);
+      if (iT < 0 || psi_off_[iT] < 0) continue;
+      const int jT = psi_rcoarse_[iT];
+      if (rcoarse(ER.coarse.q[jR] + dR) != jT) continue;
+      xl[n].push_back(XB{int(iL), jR, int(iT), jT, o});
+      if (t.L) o += int64_t(EL.coarse.dim[iT]) * ER.coarse.dim[jR];
+    }
+    xsize[n] = o;
+  }
+  std::vector<FineMap> fmL(T.size()), fmR(T.size());
+  for (size_t n = 0; n < T.size(); ++n) {
+    fmL[n] = fine_map(T[n].L);
+    fmR[n] = fine_map(T[n].R);
+  }
+  // chunks of terms: X and Y (each xsize) under the cap
+  const int64_t cap = P_.mem_cap ? std::max<int64_t>(int64_t(1) << 14, int64_t(P_.mem_cap / 16 / sizeof(double)))
+                                 : int64_t(1) << 27;
+  std::vector<std::pair<size_t, size_t>> ranges;
+  {
+    size_t s = 0;
+    int64_t acc = 0;
+    for (size_t n = 0; n < T.size(); ++n) {
+      if (acc + xsize[n] > cap && n > s) {
+        ranges.push_back({s, n});
+        s = n;
+        acc = 0;
+      }
+      acc += xsize[n];
+    }
+    ranges.push_back({s, T.size()});
+  }
+  for (auto& rg : ranges) {
+    int64_t tot = 0;
+    std::vector<int64_t> base(T.size(), 0);
+    for (size_t n = rg.first; n < rg.second; ++n) {
+      base[n] = tot;
+      tot += xsize[n];
+    }
+    double* X = static_cast<double*>(ex_->alloc(size_t(std::max<int64_t>(tot, 1)) * sizeof(double)));
+    double* Y = static_cast<double*>(ex_->alloc(size_t(std::max<int64_t>(tot, 1)) * sizeof(double)));
+    std::vector<GemmProb> P1;
+    std::vector<GemmSeg> S1;
+    // targets: C pointer -> (M, N, segments)
+    struct Acc { int M, N; std::vector<GemmSeg> segs; };
+    std::map<double*, Acc> acc;
+    auto add = [&](double* C, int M, int N, const GemmSeg& g) {
+      Acc& a = acc[C];
+      a.M = M;
+      a.N = N;
+      a.segs.push_back(g);
+    };
+    for (size_t n = rg.first; n < rg.second; ++n) {
+      const Term& t = T[n];
+      for (const XB& xb : xl[n]) {
+        const int cols = ER.coarse.dim[xb.jR], colsT = ER.coarse.dim[xb.jT], rowsT = EL.coarse.dim[xb.iT];
+        const QN qL = EL.coarse.q[xb.iL];
+        const double sg = (t.R && t.R->odd && (qL.n() & 1)) ? -1.0 : 1.0;
+        const double* ps = psi + psi_off_[xb.iL];
+        const double* lm = lam + psi_off_[xb.iT];
+        const double* Xs = ps;   // identity on L': X = psi
+        if (t.L) {
+          double* Xb = X + base[n] + xb.off;
+          double* Yb = Y + base[n] + xb.off;
+          Xs = Xb;
+          // X{iT, jR} = c s op(O_L) psi
+          for (int ft : EL.coarse_fines[xb.iT]) {
+            GemmProb q;
+            q.C = Xb + int64_t(EL.f_row[ft]) * cols;
+            q.ldc = cols;
+            q.M = EL.f_dim[ft];
+            q.N = cols;
+            q.alpha = t.c * sg;
+            q.accumulate = 0;
+            q.s0 = int(S1.size());
+            for (int f : EL.coarse_fines[xb.iL]) {
+              auto it = t.Lt ? fmL[n].find({f, ft}) : fmL[n].find({ft, f});
+              if (it == fmL[n].end()) continue;
+              const OpBlk* ob = it->second;
+              S1.push_back(GemmSeg{EopsL_.arena + ob->off, ps + int64_t(EL.f_row[f]) * cols, ob->cols, cols,
+                                   EL.f_dim[f], t.Lt, 0});
+            }
+            q.s1 = int(S1.size());
+            P1.push_back(q);
+          }
+          // Y{iT, jR} = c s lam{iT, jT} op(O_R){jT <- jR}
+          for (int g : ER.coarse_fines[xb.jR]) {
+            GemmProb q;
+            q.C = Yb + ER.f_row[g];
+            q.ldc = cols;
+            q.M = rowsT;
+            q.N = ER.f_dim[g];
+            q.alpha = t.c * sg;
+            q.accumulate = 0;
+            q.s0 = int(S1.size());
+            for (int gt : ER.coarse_fines[xb.jT]) {
+              auto it = t.Rt ? fmR[n].find({g, gt}) : fmR[n].find({gt, g});
+              if (it == fmR[n].end()) continue;
+              const OpBlk* ob = it->second;
+              S1.push_back(GemmSeg{lm + ER.f_row[gt], EopsR_.arena + ob->off, colsT, ob->cols, ER.f_dim[gt], 0, t.Rt});
+            }
+            q.s1 = int(S1.size());
+            P1.push_back(q);
+          }
+          // L' operator: fine blocks (ft <- f), or (f <- ft) stored for a transposed use
+          const OpKey kl = keyL.at(t.L);
+          for (int ft : EL.coarse_fines[xb.iT])
+            for (int f : EL.coarse_fines[xb.iL]) {
+              const double* Yr = Yb + int64_t(EL.f_row[ft]) * cols;
+              const double* Pr = ps + int64_t(EL.f_row[f]) * cols;
+              if (!t.Lt) {
+                const int64_t o = target(tl, kl, ft, f);
+                if (o >= 0) add(gl + o, EL.f_dim[ft], EL.f_dim[f], GemmSeg{Yr, Pr, cols, cols, cols, 0, 1});
+              } else {
+                const int64_t o = target(tl, kl, f, ft);
+                if (o >= 0) add(gl + o, EL.f_dim[f], EL.f_dim[ft], GemmSeg{Pr, Yr, cols, cols, cols, 0, 1});
+              }
+            }
+        }
+        // R' operator: fine blocks (gt <- g), or (g <- gt) stored for a transposed use
+        const OpKey kr = keyR.at(t.R);
+        for (int gt : ER.coarse_fines[xb.jT])
+          for (int g : ER.coarse_fines[xb.jR]) {
+            if (!t.Rt) {
+              const int64_t o = target(tr, kr, gt, g);
+              if (o >= 0)
+                add(gr + o, ER.f_dim[gt], ER.f_dim[g], GemmSeg{lm + ER.f_row[gt], Xs + ER.f_row[g], colsT, cols, rowsT, 1, 0});
+            } else {
+              const int64_t o = target(tr, kr, g, gt);
+              if (o >= 0)
+                add(gr + o, ER.f_dim[g], ER.f_dim[gt], GemmSeg{Xs + ER.f_row[g], lm + ER.f_row[gt], cols, colsT, rowsT, 1, 0});
+            }
+          }
+      }
+    }
+    if (&rg == &ranges.front()) {
+      // H_L' (x) 1: dF/dH_L'{ft <- f} = lam{i}[ft rows] psi{i}[f rows]^T
+      const Op* HL = EopsL_.get(OP_H, 0);
+      if (HL) {
+        const OpKey kh = keyL.at(HL);
+        for (size_t i = 0; i < EL.coarse.q.size(); ++i) {
+          if (psi_off_[i] < 0) continue;
+          const int cols = ER.coarse.dim[psi_rcoarse_[i]];
+          for (int ft : EL.coarse_fines[i])
+            for (int f : EL.coarse_fines[i]) {
+              const int64_t o = target(tl, kh, ft, f);
+              if (o < 0) continue;
+              add(gl + o, EL.f_dim[ft], EL.f_dim[f],
+                  GemmSeg{lam + psi_off_[i] + int64_t(EL.f_row[ft]) * cols, psi + psi_off_[i] + int64_t(EL.f_row[f]) * cols,
+                          cols, cols, cols, 0, 1});
+            }
+        }
+      }
+    }
+    if (!P1.empty()) ex_->gemm(P1, S1);
+    std::vector<GemmProb> P2;
+    std::vector<GemmSeg> S2;
+    for (auto& kv : acc) {
+      GemmProb q;
+      q.C = kv.first;
+      q.ldc = kv.second.N;
+      q.M = kv.second.M;
+      q.N = kv.second.N;
+      q.alpha = 1.0;
+      q.accumulate = 1;
+      q.s0 = int(S2.size());
+      S2.insert(S2.end(), kv.second.segs.begin(), kv.second.segs.end());
+      q.s1 = int(S2.size());
+      P2.push_back(q);
+    }
+    if (!P2.empty()) ex_->gemm(P2, S2);
+    ex_->release(X);
+    ex_->release(Y);
+  }
 }
 
 }  // namespace dmrg

@@ -47,6 +47,14 @@ struct DiagTask {
   double coef;
 };
 
+// Frobenius products for the adjoint: out = sum_{r < rows, c < cols} a[r*lda + c] *
+// (mode 0: b[r*ldb + c], mode 1: b[c*ldb + r], mode 2: 1 if r == c else 0)
+struct DotTask {
+  const double* a;
+  const double* b;
+  int lda, ldb, rows, cols, mode;
+};
+
 // ---- split-BF16 tensor-core path -------------------------------------------
 // An operand x is carried as three BF16 planes (x ~ hi + mid + lo) stored
 // together in a "blocked split matrix": for a matrix with R rows (R8 = R padded
@@ -133,6 +141,12 @@ class Exec {
   virtual void gemm_run(int plan) = 0;
   virtual void plan_free(int plan) = 0;
   virtual void diag(const std::vector<DiagTask>& t) = 0;
+  // generalised Fock matrix F_pq = sum_r t_pr g1_qr + sum_rst v_prst g2_qrst and the
+  // orbital gradient grad_pq = 2 (F_qp - F_pq) (device arrays, row-major L x L / L^4)
+  virtual void orbital_gradient(int L, const double* t, const double* v, const double* g1, const double* g2,
+                                double* grad) = 0;
+  // out[i] (device) = the Frobenius product of task i (fixed-order reductions)
+  virtual void dots(const std::vector<DotTask>& t, double* out) = 0;
 
   // dense FP64 vector kernels on length-n vectors stored with a row stride
   // out[i*ldo + j] = sum_e V[i*ldv + e] * X[j*ldx + e]     (i < m, j < k)

@@ -146,6 +146,60 @@ __global__ void __launch_bounds__(256) kron_kernel(const KronCta* __restrict__ c
   }
 }
 
+// one CTA per task (grid-stride), each thread a fixed subset of the elements, then a
+// fixed warp / block tree: the result does not depend on scheduling
+__global__ void __launch_bounds__(128) dot_tasks_kernel(const DotTask* __restrict__ t, int nt,
+                                                        double* __restrict__ out) {
+  __shared__ double red[4];
+  for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+    const DotTask d = t[i];
+    const int n = d.rows * d.cols;
+    double acc = 0.0;
+    if (d.mode == 2) {
+      for (int r = threadIdx.x; r < min(d.rows, d.cols); r += blockDim.x) acc += d.a[int64_t(r) * d.lda + r];
+    } else {
+      for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int r = e / d.cols, c = e - r * d.cols;
+        const double bv = d.mode == 0 ? d.b[int64_t(r) * d.ldb + c] : d.b[int64_t(c) * d.ldb + r];
+        acc = fma(d.a[int64_t(r) * d.lda + c], bv, acc);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) out[i] = (red[0] + red[1]) + (red[2] + red[3]);
+    __syncthreads();
+  }
+}
+
+// F_pq = sum_r t_pr g1_qr + sum_rst v_prst g2_qrst: one CTA per (p, q), the two
+// contiguous rows t[p, :] . g1[q, :] and v[p, ...] . g2[q, ...] (L + L^3 products)
+__global__ void __launch_bounds__(128) fock_kernel(int L, const double* __restrict__ t, const double* __restrict__ v,
+                                                   const double* __restrict__ g1, const double* __restrict__ g2,
+                                                   double* __restrict__ F) {
+  __shared__ double red[4];
+  const int p = blockIdx.x / L, q = blockIdx.x % L;
+  const int64_t L3 = int64_t(L) * L * L;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < L; r += blockDim.x) acc = fma(t[int64_t(p) * L + r], g1[int64_t(q) * L + r], acc);
+  const double* vp = v + p * L3;
+  const double* gq = g2 + q * L3;
+  for (int64_t e = threadIdx.x; e < L3; e += blockDim.x) acc = fma(vp[e], gq[e], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) F[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+__global__ void orbital_grad_kernel(int L, const double* __restrict__ F, double* __restrict__ g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L * L) return;
+  const int p = i / L, q = i % L;
+  g[i] = 2.0 * (F[q * L + p] - F[p * L + q]);
+}
+
 __global__ void diag_kernel(const DiagTask* __restrict__ t, int nt) {
   for (int i = blockIdx.x; i < nt; i += gridDim.x) {
     const DiagTask d = t[i];
@@ -793,6 +847,20 @@ class CudaExec : public Exec {
     int id = gemm_plan(p, s);
     gemm_run(id);
     plan_free(id);
+  }
+  void orbital_gradient(int L, const double* t, const double* v, const double* g1, const double* g2,
+                        double* grad) override {
+    double* F = static_cast<double*>(alloc(sizeof(double) * size_t(L) * L));
+    launch(PROF_VEC, [&] { fock_kernel<<<L * L, 128, 0, st_>>>(L, t, v, g1, g2, F); });
+    launch(PROF_VEC, [&] { orbital_grad_kernel<<<(L * L + 127) / 128, 128, 0, st_>>>(L, F, grad); });
+    release(F);
+  }
+  void dots(const std::vector<DotTask>& t, double* out) override {
+    if (t.empty()) return;
+    DotTask* d = upload(t);
+    const unsigned nb = unsigned(std::min<size_t>(t.size(), size_t(nsm_) * 16));
+    launch(PROF_VEC, [&] { dot_tasks_kernel<<<nb, 128, 0, st_>>>(d, int(t.size()), out); });
+    release(d);
   }
   void diag(const std::vector<DiagTask>& t) override {
     if (t.empty()) return;

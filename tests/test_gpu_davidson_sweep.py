@@ -30,7 +30,7 @@ def test_sweeps_at_full_bond_dimension_equal_fci(L, na, nb, D):
     t, v = I.synthetic_integrals(L, 51 + L)
     efci = O.fci_lowest(t, v, na, nb)[0][0]
     d = B.Dmrg(t, v, na, nb, D=D, seed=5, stream=stream())
-    e = d.sweep(2, [D, D], tol=1e-9)
+    e = d.sweep(2, [D, D], tol=1e-9, max_iter=400)
     assert abs(e[-1] - efci) < 1e-8
 
 
@@ -41,7 +41,7 @@ def test_truncated_sweeps_are_variational_and_monotone_in_D():
     es = []
     for D in (8, 16, 32):
         d = B.Dmrg(t, v, na, nb, D=D, seed=7, stream=stream())
-        es.append(d.sweep(4, [D] * 4, tol=1e-8)[-1])
+        es.append(d.sweep(4, [D] * 4, tol=1e-8, max_iter=400)[-1])
     assert all(e > efci - 1e-9 for e in es)
     assert es[0] >= es[1] - 1e-9 and es[1] >= es[2] - 1e-9
 
@@ -53,5 +53,5 @@ def test_orbital_order_is_irrelevant_without_truncation():
     e = []
     for order in (None, [5, 3, 1, 0, 2, 4]):
         d = B.Dmrg(t, v, na, nb, D=64, order=order, seed=1, stream=stream())
-        e.append(d.sweep(2, [64, 64], tol=1e-9)[-1])
+        e.append(d.sweep(2, [64, 64], tol=1e-9, max_iter=400)[-1])
     assert abs(e[0] - e[1]) < 1e-9

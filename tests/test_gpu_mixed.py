@@ -77,7 +77,7 @@ def test_mixed_sweeps_match_fp64_sweeps():
     e = {}
     for prec in (B.PREC_FP64, B.PREC_MIXED_BF16):
         d = B.Dmrg(t, v, na, nb, D=D, seed=5, precision=prec, stream=stream())
-        e[prec] = d.sweep(2, [D, D], tol=1e-8)[-1]
+        e[prec] = d.sweep(2, [D, D], tol=1e-8, max_iter=400)[-1]
         d.close()
     assert abs(e[B.PREC_FP64] - efci) < 1e-8
     assert abs(e[B.PREC_MIXED_BF16] - efci) < 1e-6
