@@ -49,24 +49,30 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 sigma steps timed beside the mixed ones")
     ap.add_argument("--cpu-sample", default="12,6,6,256", help="L,na,nb,D of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sweeps", type=int, default=0,
+    ap.add_argument("--sweeps", type=int, default=1,
                     help="also time this many full two-site sweeps at bond dimension D (fresh seeded basis)")
     ap.add_argument("--sweep-tol", type=float, default=1e-6, help="Davidson residual tolerance of the timed sweeps")
+    ap.add_argument("--refine-all", action="store_true",
+                    help="split-BF16 sweeps: FP64 refinement at every step (not only the reported one)")
     ap.add_argument("--batched", type=int, default=0,
                     help="also time the batched form on this many independent problems (L ~ U[10,20], "
                          "electrons = L with alpha/beta split within +-2, D in {256,512,1024}, seeds 100..)")
     ap.add_argument("--sweep-ramp", default="",
                     help="comma list of bond dimensions: one full sweep at each, in order, on one handle from the "
                          "seeded product-state basis (the D ramp of the headline sweep); per-sweep times and energies")
-    ap.add_argument("--compare-davidson", default="",
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the sigma step only (no sweep, no Davidson comparisons)")
+    ap.add_argument("--compare-davidson", default="32,16,16,512",
                     help="L,na,nb,D: Davidson (Diag_H) at the centre bond of a fixed seeded basis in FP64 and in "
                          "split-BF16 with FP64 refinement, same start vector; times, energies and |dE|")
-    ap.add_argument("--davidson-tol", type=float, default=1e-5)
+    ap.add_argument("--davidson-tol", type=float, default=1e-6)
     ap.add_argument("--davidson-max-iter", type=int, default=300)
     ap.add_argument("--compare-sweeps", default="",
                     help="L,na,nb,D,n_sweeps: time n full sweeps in FP64 and in split-BF16 from the same seeded "
                          "basis and report both sweep times and |dE| (mixed vs FP64)")
     a = ap.parse_args()
+    if a.no_extras:
+        a.sweeps, a.compare_davidson = 0, ""
     a.na = a.L // 2 if a.na is None else a.na
     a.nb = a.L // 2 if a.nb is None else a.nb
     a.bond = a.L // 2 - 1 if a.bond is None else a.bond
@@ -194,6 +200,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if world > 1:   # the replicas time the sigma step; the sweep and Davidson extras run at N = 1
+        args.sweeps, args.compare_davidson = 0, ""
 
     import torch
     import torch.distributed as dist
@@ -348,6 +356,11 @@ def main():
             out["cpu_baseline"] = cpu_baseline(args, flops_of)
         except Exception as e:  # pragma: no cover
             out["cpu_baseline"] = {"error": str(e)}
+    if args.compare_davidson and prec == B.PREC_MIXED_BF16 and rank == 0:
+        try:
+            out["davidson_headline"] = headline_davidson(args, B, d, bp, dev)
+        except Exception as e:  # pragma: no cover
+            out["davidson_headline"] = {"error": f"{type(e).__name__}: {e}"}
     d.close()
     if args.sweeps > 0:
         # full L->R->L sweeps from the seeded kept-product-state basis, every bond at
@@ -356,17 +369,23 @@ def main():
         ds = B.Dmrg(t, v, args.na, args.nb, D=args.D, precision=prec, seed=args.seed, stream=stream.cuda_stream)
         t0 = time.perf_counter()
         ds.profile_start()
-        energies = ds.sweep(args.sweeps, [args.D] * args.sweeps, tol=args.sweep_tol)
+        energies = ds.sweep(args.sweeps, [args.D] * args.sweeps, tol=args.sweep_tol, check=False)
         torch.cuda.synchronize()
         ts = time.perf_counter() - t0
         sprof = ds.profile_stop()
+        slog = ds.sweep_log()
         out["sweep"] = {"workload": f"{args.sweeps} full sweep(s) L->R->L of L={args.L}, {args.na}a+{args.nb}b, "
                                     f"D={args.D} at every bond, from the seeded product-state basis, "
                                     f"Davidson tol {args.sweep_tol:g}",
                         "seconds_per_sweep": round(ts / args.sweeps, 2),
                         "phases_s": {k: round(x, 2) for k, x in ds.sweep_phases().items()},
                         "kernel_s": {k: round(x["ms"] / 1e3, 2) for k, x in sprof.items() if x["launches"]},
-                        "energies": [float(x) for x in energies]}
+                        "energies": [float(x) for x in energies],
+                        "steps": len(slog),
+                        "davidson_iterations": sum(x["iters"] for x in slog),
+                        "steps_by_status": {name: sum(1 for x in slog if x["status"] == k) for k, name in
+                                            enumerate(["converged", "split_floor", "max_iter", "exhausted"])},
+                        "reported_step": {k: slog[-1][k] for k in ("iters", "status", "rnorm")} if slog else None}
         ds.close()
     # optional extra measurements; a failure is recorded in the line instead of ending the run
     extras = []
@@ -400,7 +419,7 @@ def sweep_ramp(args, B, t, v, prec, stream):
     for D in Ds:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e = d.sweep(1, [D], tol=args.sweep_tol)
+        e = d.sweep(1, [D], tol=args.sweep_tol, refine_all=args.refine_all, check=False)
         torch.cuda.synchronize()
         res["sweeps"].append({"D": D, "seconds": round(time.perf_counter() - t0, 2), "energy": float(e[0]),
                               "phases_s": {k: round(x, 2) for k, x in d.sweep_phases().items()}})
@@ -424,16 +443,47 @@ def compare_davidson(args, B, I, stream):
         d.prepare(bond)
         x = torch.tensor(B.pack_psi(bp.psi), dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
+        d.profile_start()
         t0 = time.perf_counter()
         e, it = d.davidson(bond, x.data_ptr(), tol=args.davidson_tol, max_iter=args.davidson_max_iter,
                            check=False)
         torch.cuda.synchronize()
-        res[name] = {"seconds": round(time.perf_counter() - t0, 3), "iterations": it, "energy": e,
-                     "converged": bool(d.last_status == B.OK)}
+        secs = time.perf_counter() - t0
+        kp = d.profile_stop()
+        res[name] = {"seconds": round(secs, 3), "iterations": it, "energy": e,
+                     "converged": bool(d.last_status == B.OK),
+                     "kernel_s": {k: round(v_["ms"] / 1e3, 3) for k, v_ in kp.items() if v_["launches"]}}
         d.close()
     res["abs_dE"] = abs(res["fp64"]["energy"] - res["mixed"]["energy"])
     res["speedup_mixed_vs_fp64"] = round(res["fp64"]["seconds"] / res["mixed"]["seconds"], 3)
     return res
+
+
+def headline_davidson(args, B, d, bp, dev):
+    """Diag_H at the benchmark's own bond (split-BF16 sigma with FP64 residual refinement):
+    wall seconds, iterations and kernel time split; the energy is the FP64 Rayleigh quotient
+    of the returned vector and its FP64 residual norm is at most the tolerance (convergence
+    is only declared on an exact residual)."""
+    import torch
+    x = torch.tensor(B.pack_psi(bp.psi), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    d.profile_start()
+    t0 = time.perf_counter()
+    e, it = d.davidson(args.bond, x.data_ptr(), tol=args.davidson_tol, max_iter=args.davidson_max_iter, check=False)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    kp = d.profile_stop()
+    # independent FP64 check of the returned vector: Rayleigh quotient and residual norm
+    s64 = torch.empty_like(x)
+    d.sigma_ex(args.bond, x.data_ptr(), s64.data_ptr(), B.PREC_FP64)
+    torch.cuda.synchronize()
+    rq = float((x * s64).sum() / (x * x).sum())
+    rn = float(torch.linalg.norm(s64 - rq * x) / torch.linalg.norm(x))
+    return {"workload": f"Davidson at the centre bond (k={args.bond}) of L={args.L}, {args.na}a+{args.nb}b, D={args.D} "
+                        f"(the sigma workload above), split-BF16 sigma with FP64 refinement, tol {args.davidson_tol:g}",
+            "seconds": round(secs, 3), "iterations": it, "energy": e, "converged": bool(d.last_status == B.OK),
+            "kernel_s": {k: round(v_["ms"] / 1e3, 3) for k, v_ in kp.items() if v_["launches"]},
+            "fp64_check": {"rayleigh_quotient": rq, "abs_dE": abs(rq - e), "residual_norm": rn}}
 
 
 def compare_sweeps(args, B, I, stream):
@@ -449,11 +499,15 @@ def compare_sweeps(args, B, I, stream):
         torch.cuda.synchronize()
         d = B.Dmrg(t, v, na, nb, D=D, precision=prec, seed=args.seed, stream=stream.cuda_stream)
         t0 = time.perf_counter()
-        e = d.sweep(ns, [D] * ns, tol=args.sweep_tol)
+        e = d.sweep(ns, [D] * ns, tol=args.sweep_tol, refine_all=args.refine_all, check=False)
         torch.cuda.synchronize()
         ts = time.perf_counter() - t0
+        lg = d.sweep_log()
         res[name] = {"seconds_per_sweep": round(ts / ns, 2), "energies": [float(x) for x in e],
-                     "phases_s_all_sweeps": {k: round(x, 2) for k, x in d.sweep_phases().items()}}
+                     "phases_s_all_sweeps": {k: round(x, 2) for k, x in d.sweep_phases().items()},
+                     "davidson_iterations": sum(x["iters"] for x in lg),
+                     "steps_by_status": {nm: sum(1 for x in lg if x["status"] == k) for k, nm in
+                                         enumerate(["converged", "split_floor", "max_iter", "exhausted"])}}
         d.close()
     ef, em = res["fp64"]["energies"], res["mixed"]["energies"]
     res["abs_dE_per_sweep"] = [abs(a - b) for a, b in zip(ef, em)]

@@ -152,10 +152,8 @@ dmrg_status dmrg_prepare(dmrg_handle* h, int32_t bond) {
   return guard([&]() -> dmrg_status {
     if (!h) return fail(DMRG_ERR_ARG, "null handle");
     if (bond < 0 || bond > h->L - 2) return fail(DMRG_ERR_ARG, "bond out of range");
-    if (h->left_loaded < bond && !h->eng->left_block(bond).valid)
-      return fail(DMRG_ERR_ARG, "left sites 0..bond-1 are not loaded");
-    if (h->right_loaded > bond + 2 && !h->eng->right_block(bond + 2).valid)
-      return fail(DMRG_ERR_ARG, "right sites bond+2..L-1 are not loaded");
+    if (!h->eng->left_buildable(bond)) return fail(DMRG_ERR_ARG, "left sites 0..bond-1 are not loaded");
+    if (!h->eng->right_buildable(bond + 2)) return fail(DMRG_ERR_ARG, "right sites bond+2..L-1 are not loaded");
     h->eng->build_left_blocks(bond);
     h->eng->build_right_blocks(bond + 2);
     h->eng->prepare_bond(bond);
@@ -249,7 +247,7 @@ dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_sch
       D[s] = D_schedule ? D_schedule[s] : h->eng->problem().D;
       if (D[s] <= 0) return fail(DMRG_ERR_ARG, "D must be positive");
     }
-    if (h->right_loaded > 2 && h->any_loaded && !h->eng->right_block(2).valid)
+    if (h->any_loaded && !h->eng->right_buildable(2))
       return fail(DMRG_ERR_ARG, "a partially loaded basis must reach site 2 for sweeps");
     h->eng->set_D(D[0]);
     std::vector<double> e = h->eng->run_sweeps(n_sweeps, D.data(), tol, flags, max_iter > 0 ? max_iter : 100);

@@ -181,6 +181,9 @@ class Engine {
   // isometries of sites 0..bond-1 / bond+2..L-1 (host arrays).
   void load_left(int site, const Sectors& out, const std::vector<const double*>& mats);
   void load_right(int site, const Sectors& out, const std::vector<const double*>& mats);
+  // whether B_n / C_m exists or can be built from the isometries held (loaded or swept)
+  bool left_buildable(int n) const;
+  bool right_buildable(int m) const;
   void build_left_blocks(int upto);     // B_0 .. B_upto from the loaded left isometries
   void build_right_blocks(int downto);  // C_L .. C_downto
 

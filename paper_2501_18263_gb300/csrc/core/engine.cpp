@@ -114,6 +114,22 @@ void Engine::load_right(int site, const Sectors& out, const std::vector<const do
   rb_[site].valid = false;
 }
 
+bool Engine::left_buildable(int n) const {
+  for (int k = n; k >= 0; --k) {
+    if (lb_[k].valid) return true;
+    if (k == 0 || !liso_[k - 1].valid) return false;
+  }
+  return false;
+}
+
+bool Engine::right_buildable(int m) const {
+  for (int k = m; k <= P_.L; ++k) {
+    if (rb_[k].valid) return true;
+    if (k == P_.L || !riso_[k].valid) return false;
+  }
+  return false;
+}
+
 void Engine::build_left_blocks(int upto) {
   for (int n = 0; n < upto; ++n) {
     if (lb_[n + 1].valid) continue;
@@ -741,7 +757,15 @@ void Engine::tick(int k) {
 std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol, int flags, int max_iter) {
   const int L = P_.L;
   if (L < 3) throw std::runtime_error("sweeps need L >= 3");
-  if (!psi_cur_ || bond_ != 0) init_sweep_state();
+  if (!(psi_cur_ && bond_ == 0)) {
+    // a loaded or swept basis (e.g. after new integrals) is rebuilt at bond 0; the
+    // swept wave function is kept when its layout still fits
+    if (right_buildable(2)) {
+      build_right_blocks(2);
+      prepare_bond(0);
+    }
+    if (!(psi_cur_ && bond_ == 0 && psi_cur_cap_ == psi_n_)) init_sweep_state();
+  }
   std::vector<double> E;
   sweep_log_.clear();
   for (double& x : phase_s) x = 0.0;
