@@ -247,6 +247,29 @@ dmrg_status dmrg_expectation(dmrg_handle* h, int32_t bond, const double* lam_dev
  * = 2 (F_qp - F_pq) (device, L^2 doubles, antisymmetric). */
 dmrg_status dmrg_orbital_gradient(dmrg_handle* h, const double* g1_dev, const double* g2_dev, double* grad_dev);
 
+/*
+ * Sharded sigma (several GPUs, one problem; the paper spreads the task list of a
+ * sigma step over its GPUs, Sec. 2.4 and Fig. 5): the terms of H_eff at a bond
+ * are divided among the ranks, psi is replicated, each rank computes the sum of
+ * its terms, and one sum of the partial sigmas over the ranks (an all-reduce)
+ * gives sigma.
+ *   dmrg_term_work: *n_terms and, if work != NULL, work[nu] = algorithmic flops
+ *     of term nu at `bond` (terms in the library's order; the last one is the
+ *     local term H_L' (x) 1).
+ *   dmrg_term_partition: owner[nu] in [0, world) for n terms (host only, no
+ *     device needed, deterministic: longest-work-first onto the least loaded
+ *     rank, ties to the lower index / lower rank), so every rank computes the
+ *     same partition on its own.
+ *   dmrg_sigma_subset: sigma_dev = the FP64 sum of the terms with
+ *     owner[nu] == rank (device buffers of psi_size doubles; owner host int32 of
+ *     n_terms).  The sum over all ranks equals dmrg_sigma at FP64 up to the
+ *     order of summation.
+ */
+dmrg_status dmrg_term_work(dmrg_handle* h, int32_t bond, int32_t* n_terms, int64_t* work);
+dmrg_status dmrg_term_partition(int32_t n, const int64_t* work, int32_t world, int32_t* owner);
+dmrg_status dmrg_sigma_subset(dmrg_handle* h, int32_t bond, const double* psi_dev, double* sigma_dev,
+                              const int32_t* owner, int32_t rank);
+
 /* Statistics of the prepared bond: int64[16] = psi_size, n_terms,
  * flops_stage1, flops_stage2 (algorithmic sigma flops), operator_bytes,
  * gemm_problems, gemm_segments, kernel launches of one FP64 sigma, then for the

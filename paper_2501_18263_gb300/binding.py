@@ -19,7 +19,8 @@ PREC_FP64, PREC_MIXED_BF16 = 0, 1
 
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
            "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_ex", "dmrg_sweep_log", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_set_integrals",
-           "dmrg_sweep_state", "dmrg_expectation", "dmrg_orbital_gradient", "dmrg_stats",
+           "dmrg_sweep_state", "dmrg_expectation", "dmrg_orbital_gradient", "dmrg_term_work",
+           "dmrg_term_partition", "dmrg_sigma_subset", "dmrg_stats",
            "dmrg_plan_paths", "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
            "dmrg_last_error"]
 SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
@@ -70,6 +71,9 @@ def load_library(path: str | None = None):
         "dmrg_sweep_state": ([vp, ip, i64p, vp], ctypes.c_int),
         "dmrg_expectation": ([vp, i32, vp, vp, dp], ctypes.c_int),
         "dmrg_orbital_gradient": ([vp, vp, vp, vp], ctypes.c_int),
+        "dmrg_term_work": ([vp, i32, ip, i64p], ctypes.c_int),
+        "dmrg_term_partition": ([i32, i64p, i32, ip], ctypes.c_int),
+        "dmrg_sigma_subset": ([vp, i32, vp, vp, ip, i32], ctypes.c_int),
         "dmrg_stats": ([vp, i64p], ctypes.c_int),
         "dmrg_plan_paths": ([vp, i64p], ctypes.c_int),
         "dmrg_profile": ([vp, i32, dp], ctypes.c_int),
@@ -248,6 +252,18 @@ class Dmrg:
         self._check(self.lib.dmrg_orbital_gradient(self.h, ctypes.c_void_p(int(g1_ptr)), ctypes.c_void_p(int(g2_ptr)),
                                                    ctypes.c_void_p(int(grad_ptr))))
 
+    def term_work(self, bond):
+        n = ctypes.c_int32()
+        self._check(self.lib.dmrg_term_work(self.h, bond, ctypes.byref(n), None))
+        w = np.zeros(n.value, dtype=np.int64)
+        self._check(self.lib.dmrg_term_work(self.h, bond, ctypes.byref(n), w.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return w
+
+    def sigma_subset(self, bond, psi_ptr, sig_ptr, owner, rank):
+        own = np.ascontiguousarray(owner, dtype=np.int32)
+        self._check(self.lib.dmrg_sigma_subset(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.c_void_p(int(sig_ptr)),
+                                               own.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(rank)))
+
     def profile_start(self):
         self._check(self.lib.dmrg_profile(self.h, 1, None))
 
@@ -309,6 +325,18 @@ class Batch:
             self.b = None
 
     __del__ = close
+
+
+def term_partition(work, world, lib=None):
+    """owner[nu] in [0, world) for the per-term work list (the library's deterministic partition; no device)."""
+    L = load_library(lib)
+    w = np.ascontiguousarray(work, dtype=np.int64)
+    own = np.zeros(len(w), dtype=np.int32)
+    st = L.dmrg_term_partition(len(w), w.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(world),
+                               own.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if st != OK:
+        raise DmrgError(st, L.dmrg_last_error().decode())
+    return own
 
 
 def pack_psi(blocks):

@@ -1,6 +1,7 @@
 // C ABI (include/dmrg_gb300.h) over the host core.  Every entry point catches
 // all exceptions and returns a status; messages are kept per thread.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -405,6 +406,55 @@ dmrg_status dmrg_orbital_gradient(dmrg_handle* h, const double* g1, const double
     ex->sync();
     ex->release(d);
     return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_term_work(dmrg_handle* h, int32_t bond, int32_t* n_terms, int64_t* work) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !n_terms) return fail(DMRG_ERR_ARG, "null argument");
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    const std::vector<int64_t> w = h->eng->term_work();
+    *n_terms = int32_t(w.size());
+    if (work) std::copy(w.begin(), w.end(), work);
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_term_partition(int32_t n, const int64_t* work, int32_t world, int32_t* owner) {
+  return guard([&]() -> dmrg_status {
+    if (n < 0 || world <= 0 || (n > 0 && (!work || !owner))) return fail(DMRG_ERR_ARG, "bad arguments");
+    for (int32_t i = 0; i < n; ++i)
+      if (work[i] < 0) return fail(DMRG_ERR_ARG, "negative work");
+    // longest processing time first: terms by decreasing work (ties: lower index
+    // first), each to the least loaded rank (ties: lower rank)
+    std::vector<int32_t> ord(n);
+    for (int32_t i = 0; i < n; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
+    std::vector<int64_t> load(world, 0);
+    for (int32_t i : ord) {
+      int32_t r = 0;
+      for (int32_t k = 1; k < world; ++k)
+        if (load[k] < load[r]) r = k;
+      owner[i] = r;
+      load[r] += work[i];
+    }
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_sigma_subset(dmrg_handle* h, int32_t bond, const double* psi, double* sig, const int32_t* owner,
+                              int32_t rank) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !psi || !sig || !owner) return fail(DMRG_ERR_ARG, "null argument");
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    const size_t nt = h->eng->term_work().size();
+    std::vector<char> own(nt, 0);
+    for (size_t i = 0; i < nt; ++i) own[i] = owner[i] == rank ? 1 : 0;
+    h->eng->sigma_subset(psi, sig, own);
+    h->eng->exec()->sync();
+    return check_device(h);
   });
 }
 

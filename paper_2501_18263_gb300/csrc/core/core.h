@@ -195,6 +195,10 @@ class Engine {
   const BondStats& stats() const { return st_; }
 
   void sigma(const double* psi, double* sig);                 // device pointers, FP64 path
+  // sharded sigma: per-term work (sigma_terms() order, then the local term H_L' (x) 1)
+  // and the FP64 sigma of the terms with own[nu] != 0
+  std::vector<int64_t> term_work() const;
+  void sigma_subset(const double* psi, double* sig, const std::vector<char>& own);
   void sigma_precision(const double* psi, double* sig, int precision);
   void diagonal(double* d);                                    // diag of H_eff (device)
 

@@ -1160,3 +1160,192 @@ void Engine::sigma_adjoint(const double* lam, const double* psi,
 }
 
 }  // namespace dmrg
+
+namespace dmrg {
+
+// ---- term partition for sharded sigma (several GPUs, psi replicated, one sum of
+// the partial sigmas): per-term work and the FP64 sigma of a subset of the terms.
+// Term index nu runs over sigma_terms(); the last index is the local term
+// H_L' (x) 1.
+
+std::vector<int64_t> Engine::term_work() const {
+  if (bond_ < 0) throw std::runtime_error("term_work: no bond prepared");
+  const Enlarged& EL = EL_;
+  const Enlarged& ER = ER_;
+  const std::vector<Term> T = sigma_terms();
+  std::vector<int64_t> w(T.size() + 1, 0);
+  for (size_t n = 0; n < T.size(); ++n) {
+    const Term& t = T[n];
+    const QN dL = !t.L ? QN{0, 0} : (t.Lt ? QN{0, 0} - t.L->delta : t.L->delta);
+    const QN dR = t.Rt ? QN{0, 0} - t.R->delta : t.R->delta;
+    for (size_t iL = 0; iL < EL.coarse.q.size(); ++iL) {
+      if (psi_off_[iL] < 0) continue;
+      const int jR = psi_rcoarse_[iL];
+      const int iT = EL.coarse.find(EL.coarse.q[iL] + dL);
+      if (iT < 0 || psi_off_[iT] < 0) continue;
+      const int jT = psi_rcoarse_[iT];
+      if (ER.coarse.find(ER.coarse.q[jR] + dR) != jT) continue;
+      const int64_t rows = EL.coarse.dim[iT], cols = ER.coarse.dim[jR], colsT = ER.coarse.dim[jT];
+      if (t.L) w[n] += 2 * rows * cols * EL.coarse.dim[iL];
+      w[n] += 2 * rows * colsT * cols;
+    }
+  }
+  for (size_t i = 0; i < EL.coarse.q.size(); ++i)
+    if (psi_off_[i] >= 0)
+      w[T.size()] += 2 * int64_t(EL.coarse.dim[i]) * EL.coarse.dim[i] * ER.coarse.dim[psi_rcoarse_[i]];
+  return w;
+}
+
+void Engine::sigma_subset(const double* psi, double* sig, const std::vector<char>& own) {
+  if (bond_ < 0) throw std::runtime_error("sigma_subset: no bond prepared");
+  const Enlarged& EL = EL_;
+  const Enlarged& ER = ER_;
+  const std::vector<Term> T = sigma_terms();
+  if (own.size() != T.size() + 1) throw std::runtime_error("sigma_subset: owner list does not match the terms");
+  ex_->zero(sig, size_t(psi_n_) * sizeof(double));
+  struct XB { int iL, jR, iT, jT; int64_t off; };
+  std::vector<std::vector<XB>> xl(T.size());
+  std::vector<int64_t> xsize(T.size(), 0);
+  for (size_t n = 0; n < T.size(); ++n) {
+    if (!own[n]) continue;
+    const Term& t = T[n];
+    const QN dL = !t.L ? QN{0, 0} : (t.Lt ? QN{0, 0} - t.L->delta : t.L->delta);
+    const QN dR = t.Rt ? QN{0, 0} - t.R->delta : t.R->delta;
+    int64_t o = 0;
+    for (size_t iL = 0; iL < EL.coarse.q.size(); ++iL) {
+      if (psi_off_[iL] < 0) continue;
+      const int jR = psi_rcoarse_[iL];
+      const int iT = EL.coarse.find(EL.coarse.q[iL] + dL);
+      if (iT < 0 || psi_off_[iT] < 0) continue;
+      const int jT = psi_rcoarse_[iT];
+      if (ER.coarse.find(ER.coarse.q[jR] + dR) != jT) continue;
+      xl[n].push_back(XB{int(iL), jR, int(iT), jT, o});
+      if (t.L) o += int64_t(EL.coarse.dim[iT]) * ER.coarse.dim[jR];
+    }
+    xsize[n] = o;
+  }
+  const int64_t cap = P_.mem_cap ? std::max<int64_t>(int64_t(1) << 14, int64_t(P_.mem_cap / 16 / sizeof(double)))
+                                 : int64_t(1) << 28;
+  std::vector<std::pair<size_t, size_t>> ranges;
+  {
+    size_t s = 0;
+    int64_t acc = 0;
+    for (size_t n = 0; n < T.size(); ++n) {
+      if (acc + xsize[n] > cap && n > s) {
+        ranges.push_back({s, n});
+        s = n;
+        acc = 0;
+      }
+      acc += xsize[n];
+    }
+    ranges.push_back({s, T.size()});
+  }
+  struct Sub { int M, N, ldc; std::vector<GemmSeg> segs; };
+  for (auto& rg : ranges) {
+    int64_t tot = 0;
+    std::vector<int64_t> base(T.size(), 0);
+    for (size_t n = rg.first; n < rg.second; ++n) {
+      base[n] = tot;
+      tot += xsize[n];
+    }
+    double* X = static_cast<double*>(ex_->alloc(size_t(std::max<int64_t>(tot, 1)) * sizeof(double)));
+    std::vector<GemmProb> P1;
+    std::vector<GemmSeg> S1;
+    std::map<double*, Sub> acc;   // sigma sub-block -> its segments
+    for (size_t n = rg.first; n < rg.second; ++n) {
+      if (!own[n]) continue;
+      const Term& t = T[n];
+      const FineMap fL = fine_map(t.L), fR = fine_map(t.R);
+      for (const XB& xb : xl[n]) {
+        const int cols = ER.coarse.dim[xb.jR], colsT = ER.coarse.dim[xb.jT], rowsT = EL.coarse.dim[xb.iT];
+        const QN qL = EL.coarse.q[xb.iL];
+        const double sg = (t.R && t.R->odd && (qL.n() & 1)) ? -1.0 : 1.0;
+        const double* ps = psi + psi_off_[xb.iL];
+        const double* Xs = ps;   // identity on L': X = psi
+        if (t.L) {
+          double* Xb = X + base[n] + xb.off;
+          Xs = Xb;
+          for (int ft : EL.coarse_fines[xb.iT]) {
+            GemmProb q;
+            q.C = Xb + int64_t(EL.f_row[ft]) * cols;
+            q.ldc = cols;
+            q.M = EL.f_dim[ft];
+            q.N = cols;
+            q.alpha = t.c * sg;
+            q.accumulate = 0;
+            q.s0 = int(S1.size());
+            for (int f : EL.coarse_fines[xb.iL]) {
+              auto it = t.Lt ? fL.find({f, ft}) : fL.find({ft, f});
+              if (it == fL.end()) continue;
+              S1.push_back(GemmSeg{EopsL_.arena + it->second->off, ps + int64_t(EL.f_row[f]) * cols, it->second->cols,
+                                   cols, EL.f_dim[f], t.Lt, 0});
+            }
+            q.s1 = int(S1.size());
+            P1.push_back(q);
+          }
+        }
+        // sigma{iT, gt} += X{iT, jR}[:, g] op(O_R){gt <- g}^T
+        for (int gt : ER.coarse_fines[xb.jT])
+          for (int g : ER.coarse_fines[xb.jR]) {
+            auto it = t.Rt ? fR.find({g, gt}) : fR.find({gt, g});
+            if (it == fR.end()) continue;
+            Sub& a = acc[sig + psi_off_[xb.iT] + ER.f_row[gt]];
+            a.M = rowsT;
+            a.N = ER.f_dim[gt];
+            a.ldc = colsT;
+            a.segs.push_back(GemmSeg{Xs + ER.f_row[g], EopsR_.arena + it->second->off, cols, it->second->cols,
+                                     ER.f_dim[g], 0, t.Rt ? 0 : 1});
+          }
+      }
+    }
+    if (!P1.empty()) ex_->gemm(P1, S1);
+    std::vector<GemmProb> P2;
+    std::vector<GemmSeg> S2;
+    for (auto& kv : acc) {
+      GemmProb q;
+      q.C = kv.first;
+      q.M = kv.second.M;
+      q.N = kv.second.N;
+      q.ldc = kv.second.ldc;
+      q.alpha = 1.0;
+      q.accumulate = 1;
+      q.s0 = int(S2.size());
+      S2.insert(S2.end(), kv.second.segs.begin(), kv.second.segs.end());
+      q.s1 = int(S2.size());
+      P2.push_back(q);
+    }
+    if (!P2.empty()) ex_->gemm(P2, S2);
+    ex_->release(X);
+  }
+  if (own[T.size()]) {
+    // H_L' (x) 1
+    const FineMap fm = fine_map(EopsL_.get(OP_H, 0));
+    std::vector<GemmProb> P3;
+    std::vector<GemmSeg> S3;
+    for (size_t i = 0; i < EL.coarse.q.size(); ++i) {
+      if (psi_off_[i] < 0) continue;
+      const int64_t cols = ER.coarse.dim[psi_rcoarse_[i]];
+      for (int ft : EL.coarse_fines[i]) {
+        GemmProb q;
+        q.C = sig + psi_off_[i] + int64_t(EL.f_row[ft]) * cols;
+        q.ldc = int(cols);
+        q.M = EL.f_dim[ft];
+        q.N = int(cols);
+        q.alpha = 1.0;
+        q.accumulate = 1;
+        q.s0 = int(S3.size());
+        for (int f : EL.coarse_fines[i]) {
+          auto it = fm.find({ft, f});
+          if (it == fm.end()) continue;
+          S3.push_back(GemmSeg{EopsL_.arena + it->second->off, psi + psi_off_[i] + int64_t(EL.f_row[f]) * cols,
+                               it->second->cols, int(cols), EL.f_dim[f], 0, 0});
+        }
+        q.s1 = int(S3.size());
+        if (q.s1 > q.s0) P3.push_back(q);
+      }
+    }
+    if (!P3.empty()) ex_->gemm(P3, S3);
+  }
+}
+
+}  // namespace dmrg
