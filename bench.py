@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--sweep-tol", type=float, default=1e-6, help="Davidson residual tolerance of the timed sweeps")
     ap.add_argument("--refine-all", action="store_true",
                     help="split-BF16 sweeps: FP64 refinement at every step (not only the reported one)")
+    ap.add_argument("--differentiate", default="",
+                    help="L,na,nb,D,n_sweeps: converge split-BF16 sweeps (D ramp from D/4), then time the adjoint "
+                         "(dmrg_sigma_backward: one- and two-particle densities) and the orbital gradient at the "
+                         "final state, checked by central differences of E(exp(kappa)) with h = 1e-5")
     ap.add_argument("--batched", type=int, default=0,
                     help="also time the batched form on this many independent problems (L ~ U[10,20], "
                          "electrons = L with alpha/beta split within +-2, D in {256,512,1024}, seeds 100..)")
@@ -397,6 +401,8 @@ def main():
         extras.append(("davidson_compare", lambda: compare_davidson(args, B, I, stream)))
     if args.compare_sweeps:
         extras.append(("sweep_compare", lambda: compare_sweeps(args, B, I, stream)))
+    if args.differentiate:
+        extras.append(("differentiation", lambda: differentiate(args, B, I, stream)))
     for key, fn in extras:
         try:
             out[key] = fn()
@@ -490,21 +496,32 @@ def compare_sweeps(args, B, I, stream):
     """Full sweeps of one problem in FP64 and in split-BF16 from the same seeded basis:
     wall seconds per sweep (with the Sec. 4.1 phase split) and the energy difference."""
     import torch
-    L, na, nb, D, ns = (int(x) for x in args.compare_sweeps.split(","))
+    f = args.compare_sweeps.split(",")
+    L, na, nb = int(f[0]), int(f[1]), int(f[2])
+    Ds = [int(x) for x in f[3].split("/")]
+    ns = int(f[4]) if len(f) > 4 else len(Ds)
+    Ds = (Ds + [Ds[-1]] * ns)[:ns]
+    D = Ds[-1]
     t, v = I.synthetic_integrals(L, args.seed)
-    res = {"workload": f"{ns} full sweep(s) L->R->L of L={L}, {na}a+{nb}b, D={D} at every bond, synthetic "
+    res = {"workload": f"{ns} full sweep(s) L->R->L of L={L}, {na}a+{nb}b, D per sweep {Ds}, synthetic "
                        f"integrals seed {args.seed}, same seeded product-state basis for both precisions, "
-                       f"Davidson tol {args.sweep_tol:g}"}
+                       f"Davidson tol {args.sweep_tol:g}" + (", split-BF16 refined at every step" if args.refine_all
+                                                             else "")}
     for name, prec in (("fp64", B.PREC_FP64), ("mixed", B.PREC_MIXED_BF16)):
         torch.cuda.synchronize()
         d = B.Dmrg(t, v, na, nb, D=D, precision=prec, seed=args.seed, stream=stream.cuda_stream)
-        t0 = time.perf_counter()
-        e = d.sweep(ns, [D] * ns, tol=args.sweep_tol, refine_all=args.refine_all, check=False)
-        torch.cuda.synchronize()
-        ts = time.perf_counter() - t0
-        lg = d.sweep_log()
-        res[name] = {"seconds_per_sweep": round(ts / ns, 2), "energies": [float(x) for x in e],
-                     "phases_s_all_sweeps": {k: round(x, 2) for k, x in d.sweep_phases().items()},
+        per, e, lg, ph = [], [], [], {}
+        for k in range(ns):   # one call per sweep: wall seconds of each
+            t0 = time.perf_counter()
+            e += list(d.sweep(1, [Ds[k]], tol=args.sweep_tol, refine_all=args.refine_all, check=False))
+            torch.cuda.synchronize()
+            per.append(round(time.perf_counter() - t0, 2))
+            lg += d.sweep_log()
+            for kk, x in d.sweep_phases().items():
+                ph[kk] = ph.get(kk, 0.0) + x
+        ts = sum(per)
+        res[name] = {"seconds_per_sweep": round(ts / ns, 2), "seconds_each": per, "energies": [float(x) for x in e],
+                     "phases_s_all_sweeps": {k: round(x, 2) for k, x in ph.items()},
                      "davidson_iterations": sum(x["iters"] for x in lg),
                      "steps_by_status": {nm: sum(1 for x in lg if x["status"] == k) for k, nm in
                                          enumerate(["converged", "split_floor", "max_iter", "exhausted"])}}
@@ -512,7 +529,78 @@ def compare_sweeps(args, B, I, stream):
     ef, em = res["fp64"]["energies"], res["mixed"]["energies"]
     res["abs_dE_per_sweep"] = [abs(a - b) for a, b in zip(ef, em)]
     res["speedup_mixed_vs_fp64"] = round(res["fp64"]["seconds_per_sweep"] / res["mixed"]["seconds_per_sweep"], 3)
+    res["speedup_last_sweep"] = round(res["fp64"]["seconds_each"][-1] / res["mixed"]["seconds_each"][-1], 3)
     return res
+
+
+def _rotated(t, v, p, q, h):
+    """Integrals rotated by U = exp(kappa), kappa = h (e_pq - e_qp) (a plane rotation: U is the
+    Givens matrix of angle h in the (p, q) plane), t' = U t U^T, v'_abcd = U_ai U_bj U_ck U_dl v_ijkl."""
+    U = np.eye(t.shape[0])
+    c, s = np.cos(h), np.sin(h)
+    U[p, p] = U[q, q] = c
+    U[p, q] = s
+    U[q, p] = -s
+    return U @ t @ U.T, np.einsum("ai,bj,ck,dl,ijkl->abcd", U, U, U, U, v, optimize=True)
+
+
+def differentiate(args, B, I, stream):
+    """The differentiation form at a converged state: split-BF16 sweeps with a D ramp, then
+    dmrg_sigma_backward (one- and two-particle densities by the adjoint), dmrg_orbital_gradient,
+    and central differences of E(exp(kappa)) for a few generators kappa_pq (same state)."""
+    import torch
+    L, na, nb, D, ns = (int(x) for x in args.differentiate.split(","))
+    t, v = I.synthetic_integrals(L, 5)
+    Ds = [max(16, D // 4), max(16, D // 2)] + [D] * max(1, ns - 2)
+    d = B.Dmrg(t, v, na, nb, D=D, precision=B.PREC_MIXED_BF16, seed=5, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    e = d.sweep(len(Ds), Ds, tol=1e-7, check=False)
+    torch.cuda.synchronize()
+    t_sweep = time.perf_counter() - t0
+    bond, n = d.sweep_state()
+    psi = torch.empty(n, dtype=torch.float64, device="cuda")
+    d.sweep_state(psi.data_ptr())
+    d.prepare(bond)
+    e0 = d.expectation(bond, psi.data_ptr(), psi.data_ptr())
+    g1 = torch.zeros((L, L), dtype=torch.float64, device="cuda")
+    g2 = torch.zeros((L, L, L, L), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    d.profile_start()
+    t0 = time.perf_counter()
+    d.sigma_backward(bond, psi.data_ptr(), psi.data_ptr(), g1.data_ptr(), g2.data_ptr())
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    kp = d.profile_stop()
+    grad = torch.zeros((L, L), dtype=torch.float64, device="cuda")
+    d.orbital_gradient(g1.data_ptr(), g2.data_ptr(), grad.data_ptr())
+    torch.cuda.synchronize()
+    G1, G2, GR = g1.cpu().numpy(), g2.cpu().numpy(), grad.cpu().numpy()
+    checks = []
+    h = 1e-5
+    pairs = [(1, 0), (L // 2, L // 2 - 1), (L - 1, 0), (L - 1, L // 3)]
+    for (p, q) in pairs:
+        es = []
+        for sgn in (+1, -1):
+            tr, vr = _rotated(t, v, p, q, sgn * h)
+            d.set_integrals(tr, vr)
+            d.prepare(bond)
+            es.append(d.expectation(bond, psi.data_ptr(), psi.data_ptr()))
+        fd = (es[0] - es[1]) / (2 * h)
+        checks.append({"p": p, "q": q, "analytic": float(GR[p, q]), "central_difference": fd,
+                       "abs_diff": abs(fd - float(GR[p, q]))})
+    d.set_integrals(t, v)
+    d.close()
+    return {"workload": f"L={L}, {na}a+{nb}b, split-BF16 sweeps with D = {Ds}, synthetic integrals seed 5; adjoint "
+                        f"and orbital gradient at the final state (bond {bond}, psi_size {n})",
+            "sweep_s": round(t_sweep, 2), "sweep_energies": [float(x) for x in e], "energy": e0,
+            "adjoint_s": round(t_adj, 3),
+            "adjoint_kernel_s": {k: round(x["ms"] / 1e3, 3) for k, x in kp.items() if x["launches"]},
+            "trace_g1": float(np.trace(G1)), "electrons": na + nb,
+            "energy_from_densities": float(np.sum(t * G1) + 0.5 * np.sum(v * G2)),
+            "abs_dE_densities": abs(float(np.sum(t * G1) + 0.5 * np.sum(v * G2)) - e0),
+            "orbital_gradient_norm": float(np.linalg.norm(GR)),
+            "fd_checks_h1e-5": checks,
+            "max_abs_diff_fd": max(c["abs_diff"] for c in checks)}
 
 
 def batched_bench(args, B, I):

@@ -210,6 +210,34 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
   double best = 1e300;
   int best_it = 0;
   int status = 2;
+  // second direction of a restart: the part of the previous Ritz vector orthogonal to
+  // V[0] = x, kept only when well resolved (|xp - c x| > 1e-4) and orthogonalised once
+  // more against x; with an exact W[0] its coupling comes from the exact pair
+  auto second = [&](bool exact) {
+    if (!have_prev) return;
+    double* V1 = V + n;
+    double* W1 = W + n;
+    ex_->mdot(x, n, 1, xp, n, 1, n, cf, 1);
+    ex_->d2d(V1, xp, n * sizeof(double));
+    ex_->axpy_dev(x, V1, n, cf, -1.0);
+    ex_->d2d(W1, wxp, n * sizeof(double));
+    ex_->axpy_dev(wx, W1, n, cf, -1.0);
+    ex_->mdot(V1, n, 1, V1, n, 1, n, nrm2, 1);
+    double pn2;
+    ex_->d2h(&pn2, nrm2, sizeof(double));
+    if (!(pn2 > 1e-8)) return;
+    ex_->normalize(V1, n, nrm2);
+    ex_->normalize(W1, n, nrm2);
+    ex_->mdot(V, n, 1, V1, n, 1, n, cf, 1);
+    ex_->axpy_dev(V, V1, n, cf, -1.0);
+    ex_->axpy_dev(W, W1, n, cf, -1.0);
+    ex_->mdot(V1, n, 1, V1, n, 1, n, nrm2, 1);
+    ex_->normalize(V1, n, nrm2);
+    ex_->normalize(W1, n, nrm2);
+    ex_->mdot(V, n, 2, W1, n, 1, n, Hs + 1, lds);
+    if (exact) ex_->mdot(W, n, 1, V1, n, 1, n, Hs + 1, lds);
+    m = 2;
+  };
   for (;; ++it) {
     ex_->ritz(Hs, lds, m, theta, y);
     if (it > 0) {
@@ -245,28 +273,40 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
         }
       }
     } else {
-      const bool just_refined = (it == last_refine + 1);   // r is the exact residual of x = V[0]
-      if (just_refined && rnorm <= tol) {
-        status = 0;
-        break;
-      }
+      const bool just_refined = (it == last_refine + 1);
       const double floor_m = 1e-6 * std::max(1.0, std::fabs(th));
-      const bool stalled = it - best_it >= 6;
-      const bool want = refines == 0 ? (rnorm <= floor_m || stalled) : (rnorm <= tol || stalled);
-      if (want && !just_refined && refines < 24) {
+      const bool stalled = it - best_it >= (refines == 0 ? 8 : 12);
+      const bool want = refines == 0 ? (rnorm <= floor_m || stalled) : (rnorm <= tol || (stalled && !just_refined));
+      if (want && refines < 24) {
         ++refines;
         last_refine = it;
         best = 1e300;
         best_it = it;
+        // x (and its split-BF16 sigma wx) normalised; V[0] = x with the exact W[0] = H x
         ex_->mdot(x, n, 1, x, n, 1, n, nrm2, 1);
+        ex_->normalize(x, n, nrm2);
+        ex_->normalize(wx, n, nrm2);
         ex_->d2d(V, x, n * sizeof(double));
-        ex_->normalize(V, n, nrm2);
         apply(V, W, 0);
         ex_->zero(Hs, size_t(lds) * lds * sizeof(double));
         ex_->mdot(V, n, 1, W, n, 1, n, Hs, lds);
+        // the exact residual of x decides convergence
+        ex_->d2d(theta, Hs, sizeof(double));
+        ex_->d2d(r, W, n * sizeof(double));
+        ex_->axpy_dev(V, r, n, theta, -1.0);
+        ex_->mdot(r, n, 1, r, n, 1, n, nrm2, 1);
+        double e2[2];
+        ex_->d2h(e2, sc, 2 * sizeof(double));
+        th = e2[0];
+        rnorm = std::sqrt(std::max(0.0, e2[1]));
+        if (rnorm <= tol) {
+          status = 0;
+          break;
+        }
         m = 1;
-        have_prev = false;
         exact0 = true;
+        second(true);
+        have_prev = false;
         continue;
       }
     }
@@ -280,32 +320,7 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
       ex_->d2d(Hs, theta, sizeof(double));
       m = 1;
       exact0 = false;
-      if (have_prev) {
-        double* V1 = V + n;
-        double* W1 = W + n;
-        ex_->mdot(x, n, 1, xp, n, 1, n, cf, 1);
-        ex_->d2d(V1, xp, n * sizeof(double));
-        ex_->axpy_dev(x, V1, n, cf, -1.0);
-        ex_->d2d(W1, wxp, n * sizeof(double));
-        ex_->axpy_dev(wx, W1, n, cf, -1.0);
-        ex_->mdot(V1, n, 1, V1, n, 1, n, nrm2, 1);
-        double pn2;
-        ex_->d2h(&pn2, nrm2, sizeof(double));
-        // keep the second direction only when it is well resolved (|xp - c x| > 1e-4),
-        // and orthogonalise it once more against x
-        if (pn2 > 1e-8) {
-          ex_->normalize(V1, n, nrm2);
-          ex_->normalize(W1, n, nrm2);
-          ex_->mdot(V, n, 1, V1, n, 1, n, cf, 1);
-          ex_->axpy_dev(V, V1, n, cf, -1.0);
-          ex_->axpy_dev(W, W1, n, cf, -1.0);
-          ex_->mdot(V1, n, 1, V1, n, 1, n, nrm2, 1);
-          ex_->normalize(V1, n, nrm2);
-          ex_->normalize(W1, n, nrm2);
-          ex_->mdot(V, n, 2, W1, n, 1, n, Hs + 1, lds);
-          m = 2;
-        }
-      }
+      second(false);
     }
     ex_->precond(r, diag, theta, n, t, 1e-8);
     for (int pass = 0; pass < 2; ++pass) {

@@ -169,7 +169,8 @@ def test_autograd_energy_and_orbital_gradient_by_central_differences():
     assert abs(np.trace(g1) - (na + nb)) < 1e-9          # <N> of a normalised state
     grad = torch.zeros((L, L), dtype=torch.float64, device="cuda:0")
     d.set_integrals(t, v)
-    d.orbital_gradient(to_dev(g1).data_ptr(), to_dev(g2).data_ptr(), grad.data_ptr())
+    gd1, gd2 = to_dev(g1), to_dev(g2)   # kept alive across the call: the library reads them
+    d.orbital_gradient(gd1.data_ptr(), gd2.data_ptr(), grad.data_ptr())
     grad = grad.cpu().numpy()
     h = 1e-5
     for (p, q) in [(1, 0), (5, 2), (7, 6), (6, 1)]:
