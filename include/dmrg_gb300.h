@@ -290,6 +290,14 @@ dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out16);
  * than one 128-row tile, number of terms. */
 dmrg_status dmrg_plan_paths(dmrg_handle* h, int64_t* out8);
 
+/* Sigma steps replayed from a captured CUDA graph since the handle was created.
+ * Every prepared bond captures its sigma step (split, grouped tensor-core or
+ * FP64 GEMM launches, reductions) once per precision into a CUDA graph and
+ * replays it for every Davidson iteration, when the handle's stream is a created
+ * (non-default) stream that is not being captured and kernel timing is off;
+ * otherwise the launches are issued one by one.  Results are identical. */
+dmrg_status dmrg_graph_replays(dmrg_handle* h, int64_t* replays);
+
 /* Kernel timing with CUDA events on the handle's stream (this library's
  * kernels only).  mode = 1: reset counters and start; mode = 0: stop and write
  * out14[2c] = milliseconds and out14[2c+1] = launches for the kernel classes

@@ -20,7 +20,7 @@ PREC_FP64, PREC_MIXED_BF16 = 0, 1
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
            "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_ex", "dmrg_sweep_log", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_set_integrals",
            "dmrg_sweep_state", "dmrg_expectation", "dmrg_orbital_gradient", "dmrg_term_work",
-           "dmrg_term_partition", "dmrg_sigma_subset", "dmrg_stats",
+           "dmrg_term_partition", "dmrg_sigma_subset", "dmrg_graph_replays", "dmrg_stats",
            "dmrg_plan_paths", "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
            "dmrg_last_error"]
 SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
@@ -74,6 +74,7 @@ def load_library(path: str | None = None):
         "dmrg_term_work": ([vp, i32, ip, i64p], ctypes.c_int),
         "dmrg_term_partition": ([i32, i64p, i32, ip], ctypes.c_int),
         "dmrg_sigma_subset": ([vp, i32, vp, vp, ip, i32], ctypes.c_int),
+        "dmrg_graph_replays": ([vp, i64p], ctypes.c_int),
         "dmrg_stats": ([vp, i64p], ctypes.c_int),
         "dmrg_plan_paths": ([vp, i64p], ctypes.c_int),
         "dmrg_profile": ([vp, i32, dp], ctypes.c_int),
@@ -263,6 +264,11 @@ class Dmrg:
         own = np.ascontiguousarray(owner, dtype=np.int32)
         self._check(self.lib.dmrg_sigma_subset(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.c_void_p(int(sig_ptr)),
                                                own.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(rank)))
+
+    def graph_replays(self):
+        x = ctypes.c_int64()
+        self._check(self.lib.dmrg_graph_replays(self.h, ctypes.byref(x)))
+        return x.value
 
     def profile_start(self):
         self._check(self.lib.dmrg_profile(self.h, 1, None))

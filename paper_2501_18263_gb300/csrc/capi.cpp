@@ -499,6 +499,14 @@ dmrg_status dmrg_plan_paths(dmrg_handle* h, int64_t* o) {
   });
 }
 
+dmrg_status dmrg_graph_replays(dmrg_handle* h, int64_t* replays) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !replays) return fail(DMRG_ERR_ARG, "null argument");
+    *replays = h->eng->graph_runs();
+    return DMRG_OK;
+  });
+}
+
 dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out) {
   return guard([&]() -> dmrg_status {
     if (!h) return fail(DMRG_ERR_ARG, "null handle");

@@ -195,11 +195,15 @@ class Engine {
   const BondStats& stats() const { return st_; }
 
   void sigma(const double* psi, double* sig);                 // device pointers, FP64 path
+  void sigma_body(int precision);   // kernels of one sigma, psi_in_ -> sig_out_
+  // the same, from the bond's captured graph when possible (captured on first use
+  // unless allow_capture is false: capturing instantiates a graph)
+  void sigma_run(int precision, bool allow_capture = true);
   // sharded sigma: per-term work (sigma_terms() order, then the local term H_L' (x) 1)
   // and the FP64 sigma of the terms with own[nu] != 0
   std::vector<int64_t> term_work() const;
   void sigma_subset(const double* psi, double* sig, const std::vector<char>& own);
-  void sigma_precision(const double* psi, double* sig, int precision);
+  void sigma_precision(const double* psi, double* sig, int precision, bool allow_capture = true);
   void diagonal(double* d);                                    // diag of H_eff (device)
 
   // Davidson on the current bond; psi in/out (device).  Returns energy.  Sets
@@ -253,6 +257,7 @@ class Engine {
   // tick to phase k (the stream is synchronised at every tick)
   void tick(int k);
   void set_precision(int p) { P_.precision = p; }
+  int64_t graph_runs() const { return graph_runs_; }
 
   // Batched form: the split-BF16 sigma of the prepared bond as separate steps,
   // so that the tensor-core tiles of several problems can share one grouped
@@ -316,6 +321,10 @@ class Engine {
   int mplan_hl_ = -1;
   float* part_ = nullptr;
   int nparts_ = 1;
+  // one captured CUDA graph per prepared bond and precision for the sigma steps of
+  // Davidson (psi copied into psi_in_, result read from sig_out_ around the replay)
+  int graph_[2] = {-1, -1};
+  int64_t graph_runs_ = 0;
   void free_mixed();
   // sweep state
   double* psi_cur_ = nullptr;

@@ -42,6 +42,10 @@ FineMap fine_map(const Op* o) {
 }  // namespace
 
 void Engine::free_bond() {
+  for (int& g : graph_) {
+    if (g >= 0) ex_->graph_free(g);
+    g = -1;
+  }
   for (auto& c : chunks_) {
     if (c.plan1 >= 0) ex_->plan_free(c.plan1);
     if (c.plan2 >= 0) ex_->plan_free(c.plan2);
@@ -894,23 +898,18 @@ void Engine::build_sigma_plan() {
   }
 }
 
-void Engine::sigma(const double* psi, double* sig) {
-  if (bond_ < 0) throw std::runtime_error("sigma: no bond prepared");
-  ex_->d2d(psi_in_, psi, psi_n_ * sizeof(double));
-  for (auto& c : chunks_) {
-    if (c.plan1 >= 0) ex_->gemm_run(c.plan1);
-    ex_->gemm_run(c.plan2);
-  }
-  if (plan_hl_ >= 0) ex_->gemm_run(plan_hl_);
-  ex_->d2d(sig, sig_out_, psi_n_ * sizeof(double));
-}
-
-void Engine::sigma_precision(const double* psi, double* sig, int precision) {
+// The kernels of one sigma step of the prepared bond, from psi_in_ to sig_out_;
+// replayed from a captured CUDA graph (one per bond and precision) when the
+// stream allows it, otherwise issued directly.
+void Engine::sigma_body(int precision) {
   if (precision == 0 || !mixed_ready_) {
-    sigma(psi, sig);
+    for (auto& c : chunks_) {
+      if (c.plan1 >= 0) ex_->gemm_run(c.plan1);
+      ex_->gemm_run(c.plan2);
+    }
+    if (plan_hl_ >= 0) ex_->gemm_run(plan_hl_);
     return;
   }
-  ex_->d2d(psi_in_, psi, psi_n_ * sizeof(double));
   ex_->split_run(psi_split_);
   // H_L' (x) 1 goes to part slot nparts_, summed with the first chunk's parts
   if (mplan_hl_ >= 0) ex_->mix_run(mplan_hl_);
@@ -920,7 +919,33 @@ void Engine::sigma_precision(const double* psi, double* sig, int precision) {
     ex_->mix_run(mchunks_[c].plan2);
     ex_->reduce_parts(part_, nparts_ + (c == 0 ? 1 : 0), psi_n_, shi_, slo_, c > 0);
   }
-  ex_->df_to_f64(shi_, slo_, sig, psi_n_);
+  ex_->df_to_f64(shi_, slo_, sig_out_, psi_n_);
+}
+
+void Engine::sigma_run(int precision, bool allow_capture) {
+  const int k = (precision == 0 || !mixed_ready_) ? 0 : 1;
+  if (allow_capture && graph_[k] < 0 && !ex_->profiling())
+    graph_[k] = ex_->graph_capture([&] { sigma_body(precision); });
+  if (graph_[k] >= 0 && !ex_->profiling()) {
+    ex_->graph_run(graph_[k]);
+    ++graph_runs_;
+  } else {
+    sigma_body(precision);
+  }
+}
+
+void Engine::sigma(const double* psi, double* sig) {
+  if (bond_ < 0) throw std::runtime_error("sigma: no bond prepared");
+  ex_->d2d(psi_in_, psi, psi_n_ * sizeof(double));
+  sigma_run(0);
+  ex_->d2d(sig, sig_out_, psi_n_ * sizeof(double));
+}
+
+void Engine::sigma_precision(const double* psi, double* sig, int precision, bool allow_capture) {
+  if (bond_ < 0) throw std::runtime_error("sigma: no bond prepared");
+  ex_->d2d(psi_in_, psi, psi_n_ * sizeof(double));
+  sigma_run(precision, allow_capture);
+  ex_->d2d(sig, sig_out_, psi_n_ * sizeof(double));
 }
 
 void Engine::batch_prologue(const double* psi) {

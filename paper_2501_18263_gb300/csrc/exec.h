@@ -4,6 +4,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 namespace dmrg {
@@ -199,6 +200,12 @@ class Exec {
   // timing is on (timing records events and drains them with host waits)
   virtual void* stream() const = 0;
   virtual bool profiling() const = 0;
+  // CUDA graphs of this executor's work: capture(f) records the work f issues on the
+  // stream into an instantiated graph (-1 when the stream cannot be captured: the
+  // default stream, or kernel timing on); graph_run replays it on the stream
+  virtual int graph_capture(const std::function<void()>& f) = 0;
+  virtual void graph_run(int id) = 0;
+  virtual void graph_free(int id) = 0;
   virtual int split_plan(const std::vector<SplitTask>& t) = 0;
   virtual void split_run(int plan) = 0;
   virtual void split_plan_free(int plan) = 0;

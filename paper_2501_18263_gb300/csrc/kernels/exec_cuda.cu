@@ -736,6 +736,8 @@ class CudaExec : public Exec {
     CK(cudaMemsetAsync(err_, 0, sizeof(int), st_));
   }
   ~CudaExec() override {
+    for (auto& g : graphs_)
+      if (g) cudaGraphExecDestroy(g);
     try { drain(); } catch (...) {}
     for (auto& m : marks_) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : pool_) cudaEventDestroy(e);
@@ -1036,6 +1038,42 @@ class CudaExec : public Exec {
   void reduce_parts(const float* part, int nparts, int64_t n, float* hi, float* lo, int accumulate) override {
     launch(PROF_SPLIT, [&] { launch_reduce_parts(part, nparts, n, hi, lo, accumulate, grid_for(n), st_); });
   }
+  int graph_capture(const std::function<void()>& f) override {
+    if (st_ == nullptr || prof_) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st_, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return -1;   // the caller is capturing already
+    CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+    try {
+      f();
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(st_, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      throw;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamEndCapture(st_, &g));
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t rc = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CK(rc);
+    for (size_t i = 0; i < graphs_.size(); ++i)
+      if (!graphs_[i]) {
+        graphs_[i] = ge;
+        return int(i);
+      }
+    graphs_.push_back(ge);
+    return int(graphs_.size() - 1);
+  }
+  void graph_run(int id) override { CK(cudaGraphLaunch(graphs_.at(id), st_)); }
+  void graph_free(int id) override {
+    if (id >= 0 && id < int(graphs_.size()) && graphs_[id]) {
+      cudaGraphExecDestroy(graphs_[id]);
+      graphs_[id] = nullptr;
+    }
+  }
   int device_error() override {
     int h = 0;
     CK(cudaMemcpyAsync(&h, err_, sizeof(int), cudaMemcpyDeviceToHost, st_));
@@ -1096,6 +1134,7 @@ class CudaExec : public Exec {
   int prec_;
   int dev_ = 0, nsm_ = 148;
   int64_t n_alloc_ = 0;
+  std::vector<cudaGraphExec_t> graphs_;
   double* part_ = nullptr;
   std::vector<Plan> plans_;
 };

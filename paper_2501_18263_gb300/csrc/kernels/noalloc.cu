@@ -57,7 +57,9 @@ extern "C" dmrg_status dmrg_sigma_host_noalloc(dmrg_handle* h, int32_t bond, con
     }
     dmrg::Exec* ex = h->eng->exec();
     ex->h2d(base, psi_host, size_t(n) * sizeof(double));
-    h->eng->sigma_precision(base, base + kMaxPsi, h->eng->problem().precision);
+    // replays the bond's CUDA graph if one was captured earlier; never captures one
+    // here (instantiating a graph may allocate)
+    h->eng->sigma_precision(base, base + kMaxPsi, h->eng->problem().precision, false);
     ex->d2h(sigma_host, base + kMaxPsi, size_t(n) * sizeof(double));
     // the same device status mapping as every other entry point
     return dmrg_internal_check_device(h);
