@@ -250,10 +250,11 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
     ex_->d2d(r, wx, n * sizeof(double));
     ex_->axpy_dev(x, r, n, theta, -1.0);
     ex_->mdot(r, n, 1, r, n, 1, n, nrm2, 1);
-    double h2[2];
-    ex_->d2h(h2, sc, 2 * sizeof(double));
+    double h2[9];   // theta, |r|^2, (unused), y[0]
+    ex_->d2h(h2, sc, 9 * sizeof(double));
     th = h2[0];
     rnorm = std::sqrt(std::max(0.0, h2[1]));
+    const double y0 = h2[8];
     if (rnorm < 0.9 * best) {
       best = rnorm;
       best_it = it;
@@ -274,9 +275,16 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
       }
     } else {
       const bool just_refined = (it == last_refine + 1);
+      // the split-BF16 error of a computed residual: about 1e-6 |theta| per unit weight of
+      // split-BF16 sigmas in it (all of it before a refinement or after a restart; only
+      // the weight |y_1..| of the corrections while x = V[0] carries its exact sigma)
       const double floor_m = 1e-6 * std::max(1.0, std::fabs(th));
-      const bool stalled = it - best_it >= (refines == 0 ? 8 : 12);
-      const bool want = refines == 0 ? (rnorm <= floor_m || stalled) : (rnorm <= tol || (stalled && !just_refined));
+      const double floor_c = exact0 ? floor_m * std::sqrt(std::max(0.0, 1.0 - y0 * y0)) : floor_m;
+      bool want;
+      if (refines == 0 || !exact0)
+        want = rnorm <= std::max(tol, floor_m) || it - best_it >= 8;
+      else
+        want = rnorm <= std::max(tol, 2.0 * floor_c) || (!just_refined && it - best_it >= 40);
       if (want && refines < 24) {
         ++refines;
         last_refine = it;
