@@ -171,8 +171,12 @@ dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedu
                        double* energies);
 
 /* dmrg_sweep with options: flags bit 0 = on a split-BF16 handle, refine every
- * step with FP64 sigmas (not only the reported one); max_iter = Davidson
- * iteration limit per step (<= 0: 100).  Other flag bits are rejected. */
+ * step with FP64 sigmas (not only the reported one); bit 1 = mode optimisation:
+ * after the eigensolver at every left-to-right step, the micro-step of
+ * dmrg_mode_step (the orbitals, and with them the handle's integrals, change;
+ * dmrg_get_integrals returns them, dmrg_mode_log the angles and entropies);
+ * max_iter = Davidson iteration limit per step (<= 0: 100).  Other flag bits are
+ * rejected. */
 dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,
                           double* energies, int32_t flags, int32_t max_iter);
 
@@ -281,6 +285,35 @@ dmrg_status dmrg_sigma_subset(dmrg_handle* h, int32_t bond, const double* psi_de
  * (terms are cut into chunks so that the stage-1 intermediates fit under
  * mem_cap_bytes). */
 dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out16);
+
+/*
+ * Mode optimisation (Sec. 2.2, Fig. 1).  A spin-independent rotation of the two
+ * orbitals at the sites k, k+1 of a bond by the angle theta: the new orbitals are
+ *   c~+_k = cos(theta) c+_k + sin(theta) c+_{k+1},  c~+_{k+1} = -sin(theta) c+_k + cos(theta) c+_{k+1}
+ * (U = [[c, s], [-s, c]] on chain positions k, k+1), the integrals become
+ * t' = U t U^T and v'_abcd = sum U_ai U_bj U_ck U_dl v_ijkl, and the wave function
+ * expressed in the new orbitals gives the same energy with t', v'.
+ *   dmrg_two_site_rotate: out = psi expressed in the orbitals rotated by theta at
+ *     `bond` (device, psi_size doubles each, different buffers).
+ *   dmrg_half_renyi: the half-Renyi entropy S_1/2 = 2 ln Tr sqrt(rho) of the cut
+ *     between the two sites of `bond` (rho the reduced density matrix of
+ *     B_k x site k, psi normalised inside), by the FP64 density-matrix
+ *     eigensolver of the truncation.
+ *   dmrg_mode_step: the micro-step on the state a sweep left: theta that
+ *     minimises S_1/2 (a scan of one period, then golden-section refinement;
+ *     0 when no rotation lowers it), the state rotated, the integrals rotated and
+ *     every block operator rebuilt in the same basis; *s_before, *s_after (host,
+ *     may be NULL) the entropies.
+ *   dmrg_get_integrals: the handle's current integrals in the caller's numbering
+ *     (host t: L*L, v: L^4).
+ *   dmrg_mode_log: the micro-steps of the last sweep with mode optimisation,
+ *     rows (sweep, bond, theta, S_1/2 before, S_1/2 after), library-owned.
+ */
+dmrg_status dmrg_two_site_rotate(dmrg_handle* h, int32_t bond, double theta, const double* psi_dev, double* out_dev);
+dmrg_status dmrg_half_renyi(dmrg_handle* h, int32_t bond, const double* psi_dev, double* s_half);
+dmrg_status dmrg_mode_step(dmrg_handle* h, double* theta, double* s_before, double* s_after);
+dmrg_status dmrg_get_integrals(dmrg_handle* h, double* t, double* v);
+dmrg_status dmrg_mode_log(dmrg_handle* h, int32_t* n_steps, const double** rows);
 
 /* Code paths of the prepared bond's sigma plans (an implementation detail,
  * reported so that tests can show which paths a case exercises): int64[8] =

@@ -378,6 +378,47 @@ def rotate_integrals(t, v, U):
     return U @ t @ U.T, np.einsum("ai,bj,ck,dl,ijkl->abcd", U, U, U, U, v, optimize=True)
 
 
+def rotate_state(x, L, na, nb, U, terms=60):
+    """Coefficients, in the rotated orbitals c~+_a = sum_i U_ai c+_i (U real orthogonal
+    and close to a rotation, spin independent), of the state whose determinant
+    coefficients in the old orbitals are x:  x' = exp(-K) x  with K = sum_pq kappa_pq E_pq
+    and exp(kappa) = U^T, so that <x'| H(t', v') |x'> = <x| H(t, v) |x> for the integrals
+    of rotate_integrals.  K is applied by fci_sigma with one-body matrix kappa^T (fci_sigma
+    with a non-symmetric t applies sum_ij t_ji E_ij) and no two-body part; the exponential
+    is summed as a Taylor series after scaling by 2^-s and squared back."""
+    w, V = np.linalg.eig(np.asarray(U, dtype=np.float64).T)
+    kap = np.real(V @ np.diag(np.log(w.astype(complex))) @ np.linalg.inv(V))
+    kap = 0.5 * (kap - kap.T)
+    zero_v = np.zeros((L, L, L, L))
+    nrm = float(np.abs(kap).sum(axis=0).max()) * (na + nb)
+    sc = max(0, int(np.ceil(np.log2(max(nrm, 1e-300) / 0.5)))) if nrm > 0.5 else 0
+
+    def apply(y):   # -K y / 2^sc
+        return -fci_sigma(np.ascontiguousarray(kap.T), zero_v, na, nb, y) / (2.0 ** sc)
+
+    def expo(y):
+        out = y.copy()
+        term = y.copy()
+        for n in range(1, terms + 1):
+            term = apply(term) / n
+            out = out + term
+        return out
+
+    y = np.asarray(x, dtype=np.float64).copy()
+    # exp(-K) = (exp(-K / 2^sc))^(2^sc)
+    for _ in range(2 ** sc):
+        y = expo(y)
+    return y
+
+
+def half_renyi_cut(full, L, k):
+    """S_1/2 = 2 ln Tr sqrt(rho) of sites 0..k of a state given on the 4^L local-state
+    configurations (site 0 most significant), from the singular values across the cut."""
+    M = np.asarray(full, dtype=np.float64).reshape(4 ** (k + 1), 4 ** (L - k - 1))
+    sv = np.linalg.svd(M, compute_uv=False)
+    return 2.0 * np.log(sv.sum() / np.sqrt((sv ** 2).sum()))
+
+
 def orbital_gradient(t, v, na, nb, x):
     """dE/dkappa_pq (p > q) of E(kappa) = <x| H(exp(kappa)) |x> at kappa = 0 for fixed
     determinant coefficients x, with kappa_qp = -kappa_pq; returned as the antisymmetric

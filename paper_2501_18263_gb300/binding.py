@@ -20,7 +20,8 @@ PREC_FP64, PREC_MIXED_BF16 = 0, 1
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
            "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_ex", "dmrg_sweep_log", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_set_integrals",
            "dmrg_sweep_state", "dmrg_expectation", "dmrg_orbital_gradient", "dmrg_term_work",
-           "dmrg_term_partition", "dmrg_sigma_subset", "dmrg_graph_replays", "dmrg_stats",
+           "dmrg_term_partition", "dmrg_sigma_subset", "dmrg_graph_replays", "dmrg_two_site_rotate",
+           "dmrg_half_renyi", "dmrg_mode_step", "dmrg_get_integrals", "dmrg_mode_log", "dmrg_stats",
            "dmrg_plan_paths", "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
            "dmrg_last_error"]
 SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
@@ -75,6 +76,11 @@ def load_library(path: str | None = None):
         "dmrg_term_partition": ([i32, i64p, i32, ip], ctypes.c_int),
         "dmrg_sigma_subset": ([vp, i32, vp, vp, ip, i32], ctypes.c_int),
         "dmrg_graph_replays": ([vp, i64p], ctypes.c_int),
+        "dmrg_two_site_rotate": ([vp, i32, f64, vp, vp], ctypes.c_int),
+        "dmrg_half_renyi": ([vp, i32, vp, dp], ctypes.c_int),
+        "dmrg_mode_step": ([vp, dp, dp, dp], ctypes.c_int),
+        "dmrg_get_integrals": ([vp, dp, dp], ctypes.c_int),
+        "dmrg_mode_log": ([vp, ip, ctypes.POINTER(dp)], ctypes.c_int),
         "dmrg_stats": ([vp, i64p], ctypes.c_int),
         "dmrg_plan_paths": ([vp, i64p], ctypes.c_int),
         "dmrg_profile": ([vp, i32, dp], ctypes.c_int),
@@ -184,7 +190,8 @@ class Dmrg:
             self._check(st)
         return e.value, it.value
 
-    def sweep(self, n_sweeps, D_schedule=None, tol=1e-8, refine_all=False, max_iter=100, check=True):
+    def sweep(self, n_sweeps, D_schedule=None, tol=1e-8, refine_all=False, max_iter=100, check=True,
+              mode_opt=False):
         """Energies of n_sweeps sweeps; with check=False a DMRG_ERR_NOCONV status is kept in
         self.last_status instead of raised (the energies are written either way)."""
         e = np.zeros(n_sweeps)
@@ -193,7 +200,8 @@ class Dmrg:
             Ds = np.ascontiguousarray(D_schedule, dtype=np.int32)
         st = self.lib.dmrg_sweep_ex(self.h, n_sweeps,
                                     Ds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if Ds is not None else None,
-                                    float(tol), _dp(e), 1 if refine_all else 0, int(max_iter))
+                                    float(tol), _dp(e), (1 if refine_all else 0) | (2 if mode_opt else 0),
+                                    int(max_iter))
         self.last_status = st
         if check or st not in (OK, ERR_NOCONV):
             self._check(st)
@@ -264,6 +272,34 @@ class Dmrg:
         own = np.ascontiguousarray(owner, dtype=np.int32)
         self._check(self.lib.dmrg_sigma_subset(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.c_void_p(int(sig_ptr)),
                                                own.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(rank)))
+
+    def two_site_rotate(self, bond, theta, psi_ptr, out_ptr):
+        self._check(self.lib.dmrg_two_site_rotate(self.h, bond, float(theta), ctypes.c_void_p(int(psi_ptr)),
+                                                  ctypes.c_void_p(int(out_ptr))))
+
+    def half_renyi(self, bond, psi_ptr):
+        x = ctypes.c_double()
+        self._check(self.lib.dmrg_half_renyi(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.byref(x)))
+        return x.value
+
+    def mode_step(self):
+        th, s0, s1 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.dmrg_mode_step(self.h, ctypes.byref(th), ctypes.byref(s0), ctypes.byref(s1)))
+        return th.value, s0.value, s1.value
+
+    def get_integrals(self):
+        t = np.zeros((self.L, self.L))
+        v = np.zeros((self.L,) * 4)
+        self._check(self.lib.dmrg_get_integrals(self.h, _dp(t), _dp(v)))
+        return t, v
+
+    def mode_log(self):
+        n = ctypes.c_int32()
+        rows = ctypes.POINTER(ctypes.c_double)()
+        self._check(self.lib.dmrg_mode_log(self.h, ctypes.byref(n), ctypes.byref(rows)))
+        R = np.ctypeslib.as_array(rows, shape=(n.value * 5,)).reshape(-1, 5).copy() if n.value else np.zeros((0, 5))
+        return [dict(sweep=int(r[0]), bond=int(r[1]), theta=float(r[2]), s_before=float(r[3]), s_after=float(r[4]))
+                for r in R]
 
     def graph_replays(self):
         x = ctypes.c_int64()

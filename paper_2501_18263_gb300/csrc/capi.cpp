@@ -30,6 +30,22 @@ bool finite(const double* p, size_t n) {
 
 dmrg_status check_device(dmrg_handle* h) { return dmrg_internal_check_device(h); }
 
+// the handle's integrals in the caller's numbering from the engine's chain-order ones
+// (after orbital rotations of the mode optimisation)
+void sync_user_integrals(dmrg_handle* h) {
+  const int L = h->L;
+  const std::vector<int>& o = h->eng->problem().ord;
+  const std::vector<double>& tc = h->eng->chain_t();
+  const std::vector<double>& vc = h->eng->chain_v();
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j) h->t_user[size_t(o[i]) * L + o[j]] = tc[size_t(i) * L + j];
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j)
+      for (int k = 0; k < L; ++k)
+        for (int l = 0; l < L; ++l)
+          h->v_user[((size_t(o[i]) * L + o[j]) * L + o[k]) * L + o[l]] = vc[((size_t(i) * L + j) * L + k) * L + l];
+}
+
 // integrals in the caller's numbering -> chain order (position i holds orbital ord[i])
 void to_chain(int L, const std::vector<int>& ord, const double* t, const double* v, std::vector<double>& tc,
               std::vector<double>& vc) {
@@ -242,7 +258,7 @@ dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_sch
     if (!h || n_sweeps <= 0) return fail(DMRG_ERR_ARG, "bad arguments");
     if (h->L < 3) return fail(DMRG_ERR_ARG, "sweeps need L >= 3");
     if (!(tol > 0)) return fail(DMRG_ERR_ARG, "tol must be positive");
-    if (flags & ~1) return fail(DMRG_ERR_ARG, "unknown sweep flags");
+    if (flags & ~3) return fail(DMRG_ERR_ARG, "unknown sweep flags");
     std::vector<int> D(n_sweeps);
     for (int s = 0; s < n_sweeps; ++s) {
       D[s] = D_schedule ? D_schedule[s] : h->eng->problem().D;
@@ -253,6 +269,7 @@ dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_sch
     h->eng->set_D(D[0]);
     std::vector<double> e = h->eng->run_sweeps(n_sweeps, D.data(), tol, flags, max_iter > 0 ? max_iter : 100);
     h->eng->exec()->sync();
+    if (flags & 2) sync_user_integrals(h);
     if (energies)
       for (int s = 0; s < n_sweeps; ++s) energies[s] = e[s];
     dmrg_status ds = check_device(h);
@@ -405,6 +422,60 @@ dmrg_status dmrg_orbital_gradient(dmrg_handle* h, const double* g1, const double
     ex->orbital_gradient(L, d, d + L2, g1, g2, grad);
     ex->sync();
     ex->release(d);
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_two_site_rotate(dmrg_handle* h, int32_t bond, double theta, const double* psi, double* out) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !psi || !out) return fail(DMRG_ERR_ARG, "null argument");
+    if (psi == out) return fail(DMRG_ERR_ARG, "psi and out must be different buffers");
+    if (!std::isfinite(theta)) return fail(DMRG_ERR_ARG, "theta must be finite");
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    h->eng->rotate_two_site(theta, psi, out);
+    h->eng->exec()->sync();
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_half_renyi(dmrg_handle* h, int32_t bond, const double* psi, double* s_half) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !psi || !s_half) return fail(DMRG_ERR_ARG, "null argument");
+    dmrg_status s = ensure_bond(h, bond);
+    if (s != DMRG_OK) return s;
+    *s_half = h->eng->half_renyi(psi);
+    return check_device(h);
+  });
+}
+
+dmrg_status dmrg_mode_step(dmrg_handle* h, double* theta, double* s_before, double* s_after) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !theta) return fail(DMRG_ERR_ARG, "null argument");
+    if (!h->eng->sweep_psi() || h->eng->bond() < 0) return fail(DMRG_ERR_ARG, "no swept state (call dmrg_sweep first)");
+    *theta = h->eng->mode_step(s_before, s_after);
+    sync_user_integrals(h);
+    return check_device(h);
+  });
+}
+
+dmrg_status dmrg_get_integrals(dmrg_handle* h, double* t, double* v) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !t || !v) return fail(DMRG_ERR_ARG, "null argument");
+    std::copy(h->t_user.begin(), h->t_user.end(), t);
+    std::copy(h->v_user.begin(), h->v_user.end(), v);
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_mode_log(dmrg_handle* h, int32_t* n, const double** rows) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !n || !rows) return fail(DMRG_ERR_ARG, "null argument");
+    h->log_rows.clear();
+    for (const auto& m : h->eng->mode_log_)
+      for (double x : {double(m.sweep), double(m.bond), m.theta, m.s_before, m.s_after}) h->log_rows.push_back(x);
+    *n = int32_t(h->eng->mode_log_.size());
+    *rows = h->log_rows.data();
     return DMRG_OK;
   });
 }

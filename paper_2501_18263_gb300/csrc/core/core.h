@@ -214,7 +214,8 @@ class Engine {
   double davidson(double* psi, double tol, int max_iter, int max_sub, int* iters_out, int refine);
 
   // sweeps.  flags bit 0: FP64 refinement at every step of a split-BF16 sweep
-  // (otherwise only at the step whose energy is reported)
+  // (otherwise only at the step whose energy is reported); bit 1: mode
+  // optimisation micro-step after the eigensolver at every left-to-right step
   void init_sweep_state();
   std::vector<double> run_sweeps(int n, const int* Dsched, double tol, int flags = 0, int max_iter = 100);
 
@@ -236,6 +237,22 @@ class Engine {
   void set_integrals(const std::vector<double>& t, const std::vector<double>& v);
   // wave function of the last sweep (device, at bond(); nullptr before a sweep)
   const double* sweep_psi() const { return psi_cur_; }
+
+  // mode optimisation (Sec. 2.2, Fig. 1; modeopt.cpp): psi in the orbitals rotated
+  // by theta at the two sites of the prepared bond; the half-Renyi entropy of the
+  // cut between them; the angle that minimises it; the micro-step on the swept
+  // state (rotate psi and the integrals, rebuild the operators); returns theta
+  void rotate_two_site(double theta, const double* in, double* out);
+  std::vector<double> left_spectrum(const double* psi);
+  double half_renyi(const double* psi);
+  double entropy_at(double theta, const double* psi, double* scratch);
+  double best_rotation(const double* psi, double* s_min, double* s0);
+  void rotate_integrals_pair(int k, double theta);
+  double mode_step(double* s_before, double* s_after);
+  const std::vector<double>& chain_t() const { return P_.t; }
+  const std::vector<double>& chain_v() const { return P_.v; }
+  struct ModeLog { int sweep, bond; double theta, s_before, s_after; };
+  std::vector<ModeLog> mode_log_;
 
   double last_energy = 0.0;
   double last_rnorm = 0.0;

@@ -791,6 +791,7 @@ std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol, i
   }
   std::vector<double> E;
   sweep_log_.clear();
+  mode_log_.clear();
   for (double& x : phase_s) x = 0.0;
   ex_->sync();
   t_last_ = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -806,6 +807,14 @@ std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol, i
     auto step = [&](int b, int ltr, int refine) {
       e = davidson(psi_cur_, tol, max_iter, 24, &iters, refine);
       tick(1);
+      if ((flags & 2) && ltr) {
+        // mode optimisation micro-step: rotate the two sites' orbitals to lower the
+        // entropy of the cut, the energy unchanged
+        ModeLog ml{s, b, 0.0, 0.0, 0.0};
+        ml.theta = mode_step(&ml.s_before, &ml.s_after);
+        mode_log_.push_back(ml);
+        tick(3);
+      }
       StepLog lg{s, b, ltr, e, iters, last_status, last_rnorm, 0.0, {}};
       truncate_and_move(ltr != 0, D, &lg.discarded, &lg.kept);
       sweep_log_.push_back(std::move(lg));

@@ -344,3 +344,43 @@ def test_oracle_dmrg_is_invariant_under_rotations_of_a_complete_initial_basis():
         assert -1e-15 <= x["discarded"] <= 1.0
     full = O.dmrg_two_site(t, v, na, nb, 4 ** 3, 1, return_log=True)[1]
     assert all(abs(x["discarded"]) < 1e-14 for x in full)
+
+
+def _pair_rotation(L, k, theta):
+    U = np.eye(L)
+    c, s = np.cos(theta), np.sin(theta)
+    U[k, k], U[k, k + 1], U[k + 1, k], U[k + 1, k + 1] = c, s, -s, c
+    return U
+
+
+def test_rotate_state_keeps_the_energy_and_matches_the_one_electron_closed_form():
+    """Orbital rotations (Sec. 2.2): expressing a state in the rotated orbitals and
+    rotating the integrals leaves every expectation value of H unchanged; with one
+    electron the new coefficients are U C; the norm is kept."""
+    L, na, nb = 5, 2, 1
+    t, v = I.synthetic_integrals(L, 131)
+    rng = np.random.default_rng(132)
+    x = rng.standard_normal(O.fci_dim(L, na, nb))
+    x /= np.linalg.norm(x)
+    for U in (_pair_rotation(L, 1, 0.37), _pair_rotation(L, 3, -1.2), O.expm_skew(0.3 * (lambda a: a - a.T)(rng.standard_normal((L, L))))):
+        xr = O.rotate_state(x, L, na, nb, U)
+        tr, vr = O.rotate_integrals(t, v, U)
+        e0 = x @ O.fci_sigma(t, v, na, nb, x)
+        e1 = xr @ O.fci_sigma(tr, vr, na, nb, xr)
+        assert abs(np.linalg.norm(xr) - 1.0) < 1e-12
+        assert abs(e1 - e0) < 1e-11 * max(1.0, abs(e0))
+    # one alpha electron: coefficients over the orbitals transform as U C
+    c1 = rng.standard_normal(L)
+    U = _pair_rotation(L, 2, 0.8)
+    x1 = np.kron(c1, np.ones(1))          # (na, nb) = (1, 0): one determinant per orbital
+    np.testing.assert_allclose(O.rotate_state(x1, L, 1, 0, U), U @ c1, atol=1e-13)
+
+
+def test_half_renyi_cut_of_a_product_state_is_zero_and_of_a_bell_pair_is_ln2():
+    L = 3
+    e = np.zeros(4 ** L)
+    e[2 * 16 + 1 * 4 + 0] = 1.0          # product of local states (alpha, beta, empty)
+    assert abs(O.half_renyi_cut(e, L, 0)) < 1e-13
+    b = np.zeros(4 ** L)
+    b[2 * 16 + 0] = b[0 * 16 + 2 * 4] = 1 / np.sqrt(2)   # (alpha, empty) + (empty, alpha) on sites 0, 1
+    assert abs(O.half_renyi_cut(b, L, 0) - 2 * np.log(np.sqrt(2))) < 1e-13
