@@ -58,6 +58,9 @@ def parse():
                     help="L,na,nb,D,n_sweeps: converge split-BF16 sweeps (D ramp from D/4), then time the adjoint "
                          "(dmrg_sigma_backward: one- and two-particle densities) and the orbital gradient at the "
                          "final state, checked by central differences of E(exp(kappa)) with h = 1e-5")
+    ap.add_argument("--batched-davidson", type=int, default=0,
+                    help="with --batched: for the first n problems, Davidson at the centre bond in FP64 and in "
+                         "split-BF16 with refinement from the same start vector (per-problem |dE| and seconds)")
     ap.add_argument("--batched", type=int, default=0,
                     help="also time the batched form on this many independent problems (L ~ U[10,20], "
                          "electrons = L with alpha/beta split within +-2, D in {256,512,1024}, seeds 100..)")
@@ -666,9 +669,42 @@ def batched_bench(args, B, I):
         d.sigma_ex(b, x.data_ptr(), s.data_ptr(), B.PREC_FP64)
         de.append(abs(em - float((x * s).sum())))
     batch.close()
+    dav = []
+    for i in range(min(args.batched_davidson, n)):
+        d, b, x0 = ds[i], bonds[i], psis[i]
+        rec = {"problem": i, "L": meta[i][0], "D": meta[i][3]}
+        for name, prec in (("fp64", B.PREC_FP64), ("mixed", B.PREC_MIXED_BF16)):
+            x = x0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if prec == B.PREC_FP64:
+                # the FP64 solve on its own handle (same integrals, basis and start vector)
+                L_, na_, nb_, D_, seed_ = I.batched_problem(i)
+                t_, v_ = I.synthetic_integrals(L_, seed_)
+                bp_ = I.bond_problem(L_, na_, nb_, D_, b, seed=seed_ + 1000)
+                d64 = B.Dmrg(t_, v_, na_, nb_, D=D_, seed=seed_, stream=stream.cuda_stream)
+                d64.load_bond_problem(bp_)
+                d64.prepare(b)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                e, it = d64.davidson(b, x.data_ptr(), tol=args.davidson_tol, max_iter=args.davidson_max_iter,
+                                     check=False)
+                torch.cuda.synchronize()
+                d64.close()
+            else:
+                e, it = d.davidson(b, x.data_ptr(), tol=args.davidson_tol, max_iter=args.davidson_max_iter,
+                                   check=False)
+                torch.cuda.synchronize()
+            rec[name] = {"energy": e, "iterations": it, "seconds": round(time.perf_counter() - t0, 3)}
+        rec["abs_dE"] = abs(rec["fp64"]["energy"] - rec["mixed"]["energy"])
+        dav.append(rec)
     for d in ds:
         d.close()
-    return {"workload": f"{n} independent problems, problem i: seed 100+i, L ~ U[10,20], electrons = L with "
+    extra = {}
+    if dav:
+        extra["davidson_per_problem"] = dav
+        extra["davidson_max_abs_dE"] = max(r["abs_dE"] for r in dav)
+    return {**extra, "workload": f"{n} independent problems, problem i: seed 100+i, L ~ U[10,20], electrons = L with "
                         f"alpha-beta in {{-2..2}}, D in {{256,512,1024}}, centre bond, synthetic integrals",
             "problems": n, "flops_per_step": flops,
             "problems_per_s": {"one_by_one": round(n / t_seq, 1), "batched": round(n / t_eager, 1),

@@ -206,7 +206,8 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
   // corrections carry only the small error of their own small coefficients.
   const bool mixed = (prec != 0 && refine);
   int refines = 0, last_refine = -100;
-  bool exact0 = false;   // V[0], W[0] are an exact FP64 pair
+  bool exact0 = false;   // W[0] is an FP64 sigma of V[0], up to the error w0err
+  double w0err = 0.0;
   double best = 1e300;
   int best_it = 0;
   int status = 2;
@@ -279,7 +280,7 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
       // split-BF16 sigmas in it (all of it before a refinement or after a restart; only
       // the weight |y_1..| of the corrections while x = V[0] carries its exact sigma)
       const double floor_m = 1e-6 * std::max(1.0, std::fabs(th));
-      const double floor_c = exact0 ? floor_m * std::sqrt(std::max(0.0, 1.0 - y0 * y0)) : floor_m;
+      const double floor_c = exact0 ? w0err + floor_m * std::sqrt(std::max(0.0, 1.0 - y0 * y0)) : floor_m;
       bool want;
       if (refines == 0 || !exact0)
         want = rnorm <= std::max(tol, floor_m) || it - best_it >= 8;
@@ -313,6 +314,7 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
         }
         m = 1;
         exact0 = true;
+        w0err = 0.0;
         second(true);
         have_prev = false;
         continue;
@@ -327,8 +329,10 @@ double Engine::davidson(double* psi, double tol, int max_iter, int max_sub, int*
       ex_->zero(Hs, size_t(lds) * lds * sizeof(double));
       ex_->d2d(Hs, theta, sizeof(double));
       m = 1;
-      exact0 = false;
-      second(false);
+      // after a refinement the restart pair (x, wx) keeps W[0] = H x up to the split-BF16
+      // error of its correction components, which the floor carries on
+      if (exact0 && prec != 0) w0err += 1e-6 * std::max(1.0, std::fabs(th)) * std::sqrt(std::max(0.0, 1.0 - y0 * y0));
+      second(exact0 && prec != 0);
     }
     ex_->precond(r, diag, theta, n, t, 1e-8);
     for (int pass = 0; pass < 2; ++pass) {
