@@ -175,6 +175,13 @@ dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedu
  * after the eigensolver at every left-to-right step, the micro-step of
  * dmrg_mode_step (the orbitals, and with them the handle's integrals, change;
  * dmrg_get_integrals returns them, dmrg_mode_log the angles and entropies);
+ * bit 2 = one layer pair of swap gates (the brick-wall permutations of global
+ * mode optimisation, Sec. 2.2 and Fig. 2: Walecki's construction, every pair of
+ * modes adjacent once in L/2 such sweeps): the two modes of every even bond are
+ * exchanged when the bond is first visited and those of every odd bond on the
+ * way back (a rotation by pi/2; no eigensolver at those steps; the state is
+ * truncated to D after the swap as after any step), and the energy reported for
+ * a swap step is that of the last eigensolver;
  * max_iter = Davidson iteration limit per step (<= 0: 100).  Other flag bits are
  * rejected. */
 dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,

@@ -191,7 +191,7 @@ class Dmrg:
         return e.value, it.value
 
     def sweep(self, n_sweeps, D_schedule=None, tol=1e-8, refine_all=False, max_iter=100, check=True,
-              mode_opt=False):
+              mode_opt=False, swap_layers=False):
         """Energies of n_sweeps sweeps; with check=False a DMRG_ERR_NOCONV status is kept in
         self.last_status instead of raised (the energies are written either way)."""
         e = np.zeros(n_sweeps)
@@ -200,7 +200,7 @@ class Dmrg:
             Ds = np.ascontiguousarray(D_schedule, dtype=np.int32)
         st = self.lib.dmrg_sweep_ex(self.h, n_sweeps,
                                     Ds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if Ds is not None else None,
-                                    float(tol), _dp(e), (1 if refine_all else 0) | (2 if mode_opt else 0),
+                                    float(tol), _dp(e), (1 if refine_all else 0) | (2 if mode_opt else 0) | (4 if swap_layers else 0),
                                     int(max_iter))
         self.last_status = st
         if check or st not in (OK, ERR_NOCONV):

@@ -258,7 +258,7 @@ dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_sch
     if (!h || n_sweeps <= 0) return fail(DMRG_ERR_ARG, "bad arguments");
     if (h->L < 3) return fail(DMRG_ERR_ARG, "sweeps need L >= 3");
     if (!(tol > 0)) return fail(DMRG_ERR_ARG, "tol must be positive");
-    if (flags & ~3) return fail(DMRG_ERR_ARG, "unknown sweep flags");
+    if (flags & ~7) return fail(DMRG_ERR_ARG, "unknown sweep flags");
     std::vector<int> D(n_sweeps);
     for (int s = 0; s < n_sweeps; ++s) {
       D[s] = D_schedule ? D_schedule[s] : h->eng->problem().D;
@@ -269,7 +269,7 @@ dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_sch
     h->eng->set_D(D[0]);
     std::vector<double> e = h->eng->run_sweeps(n_sweeps, D.data(), tol, flags, max_iter > 0 ? max_iter : 100);
     h->eng->exec()->sync();
-    if (flags & 2) sync_user_integrals(h);
+    if (flags & 6) sync_user_integrals(h);
     if (energies)
       for (int s = 0; s < n_sweeps; ++s) energies[s] = e[s];
     dmrg_status ds = check_device(h);

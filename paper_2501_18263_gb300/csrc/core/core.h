@@ -215,7 +215,9 @@ class Engine {
 
   // sweeps.  flags bit 0: FP64 refinement at every step of a split-BF16 sweep
   // (otherwise only at the step whose energy is reported); bit 1: mode
-  // optimisation micro-step after the eigensolver at every left-to-right step
+  // optimisation micro-step after the eigensolver at every left-to-right step;
+  // bit 2: a layer of swap gates on each half sweep (even bonds when first
+  // visited, odd bonds on the way back), diagonalisation omitted there
   void init_sweep_state();
   std::vector<double> run_sweeps(int n, const int* Dsched, double tol, int flags = 0, int max_iter = 100);
 
@@ -249,6 +251,7 @@ class Engine {
   double best_rotation(const double* psi, double* s_min, double* s0);
   void rotate_integrals_pair(int k, double theta);
   double mode_step(double* s_before, double* s_after);
+  void apply_rotation(double theta);   // rotate the swept state and the integrals at bond()
   const std::vector<double>& chain_t() const { return P_.t; }
   const std::vector<double>& chain_v() const { return P_.v; }
   struct ModeLog { int sweep, bond; double theta, s_before, s_after; };

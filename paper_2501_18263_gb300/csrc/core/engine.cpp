@@ -809,6 +809,20 @@ std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol, i
     // reported (the last step), and at every step with refine_all; the other
     // steps stop at the split-BF16 residual floor
     auto step = [&](int b, int ltr, int refine) {
+      // swap-gate layers (the brick-wall permutations of global mode optimisation):
+      // even bonds on their first visit, odd bonds on the way back; the rotation by
+      // pi/2 exchanges the two modes, and no eigensolver runs at that step
+      const bool swap = (flags & 4) && ((b % 2 == 0) ? (ltr || b == L - 2) : !ltr);
+      if (swap) {
+        const double half_pi = 1.57079632679489661923;
+        apply_rotation(half_pi);
+        mode_log_.push_back(ModeLog{s, b, half_pi, 0.0, 0.0});
+        tick(3);
+        StepLog lg{s, b, ltr, e, 0, 0, 0.0, 0.0, {}};
+        truncate_and_move(ltr != 0, D, &lg.discarded, &lg.kept);
+        sweep_log_.push_back(std::move(lg));
+        return;
+      }
       e = davidson(psi_cur_, tol, max_iter, 24, &iters, refine);
       tick(1);
       if ((flags & 2) && ltr) {

@@ -296,21 +296,25 @@ void Engine::rotate_integrals_pair(int k, double theta) {
   set_integrals(t2, cur);
 }
 
+void Engine::apply_rotation(double theta) {
+  if (bond_ < 0 || !psi_cur_) throw std::runtime_error("apply_rotation: no swept state");
+  if (theta == 0.0) return;
+  const int b = bond_;
+  double* tmp = static_cast<double*>(ex_->alloc(size_t(psi_n_) * sizeof(double)));
+  rotate_two_site(theta, psi_cur_, tmp);
+  ex_->d2d(psi_cur_, tmp, size_t(psi_n_) * sizeof(double));
+  ex_->release(tmp);
+  rotate_integrals_pair(b, theta);
+  build_left_blocks(b);
+  build_right_blocks(b + 2);
+  prepare_bond(b);
+}
+
 double Engine::mode_step(double* s_before, double* s_after) {
   if (bond_ < 0 || !psi_cur_) throw std::runtime_error("mode_step: no swept state");
-  const int b = bond_;
   double smin = 0.0, s0 = 0.0;
   const double theta = best_rotation(psi_cur_, &smin, &s0);
-  if (theta != 0.0) {
-    double* tmp = static_cast<double*>(ex_->alloc(size_t(psi_n_) * sizeof(double)));
-    rotate_two_site(theta, psi_cur_, tmp);
-    ex_->d2d(psi_cur_, tmp, size_t(psi_n_) * sizeof(double));
-    ex_->release(tmp);
-    rotate_integrals_pair(b, theta);
-    build_left_blocks(b);
-    build_right_blocks(b + 2);
-    prepare_bond(b);
-  }
+  apply_rotation(theta);
   if (s_before) *s_before = s0;
   if (s_after) *s_after = smin;
   return theta;

@@ -110,3 +110,35 @@ def test_sweeps_with_mode_optimisation_stay_variational():
     t2, v2 = d.get_integrals()
     assert abs(O.fci_lowest(t2, v2, na, nb)[0][0] - efci) < 1e-9   # same spectrum
     d.close()
+
+
+def test_swap_layers_permute_the_modes_and_bring_every_pair_together():
+    """Swap-gate layers (Sec. 2.2, Fig. 2): at full bond dimension the swaps are exact, so
+    the sweeps keep the full-CI energy; the integrals become those of the modes permuted by
+    the swaps (each swap at positions k, k+1 is the rotation by pi/2); and over L/2 layered
+    sweeps every pair of modes is adjacent in at least one of the permutations (Walecki's
+    construction)."""
+    import torch
+    L, na, nb, D = 6, 3, 2, 64
+    t, v = I.synthetic_integrals(L, 170)
+    efci = O.fci_lowest(t, v, na, nb)[0][0]
+    d = B.Dmrg(t, v, na, nb, D=D, seed=8, stream=stream())
+    d.sweep(1, [D], tol=1e-10, max_iter=400)
+    P = np.eye(L)
+    order = list(range(L))
+    cover = {frozenset((order[a], order[a + 1])) for a in range(L - 1)}
+    for _ in range(L // 2):
+        e = d.sweep(1, [D], tol=1e-10, max_iter=400, swap_layers=True)
+        assert abs(e[-1] - efci) < 1e-8
+        for m in d.mode_log():
+            k = m["bond"]
+            assert abs(m["theta"] - np.pi / 2) < 1e-15
+            P = _pair(L, k, np.pi / 2) @ P
+            order[k], order[k + 1] = order[k + 1], order[k]
+        cover |= {frozenset((order[a], order[a + 1])) for a in range(L - 1)}
+    t2, v2 = d.get_integrals()
+    tr, vr = O.rotate_integrals(t, v, P)
+    np.testing.assert_allclose(t2, tr, atol=1e-13)
+    np.testing.assert_allclose(v2, vr, atol=1e-13)
+    assert len(cover) == L * (L - 1) // 2
+    d.close()
