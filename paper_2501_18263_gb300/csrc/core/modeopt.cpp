@@ -140,16 +140,20 @@ void Engine::rotate_two_site(double theta, const double* in, double* out) {
 
 std::vector<double> Engine::left_spectrum(const double* psi) {
   if (bond_ < 0) throw std::runtime_error("left_spectrum: no bond prepared");
+  // the nonzero eigenvalues of rho = psi psi^T are those of the smaller Gram matrix of
+  // each psi block (psi psi^T or psi^T psi): no structural zeros, whose rounding would
+  // otherwise add about sqrt(eps) each to Tr sqrt(rho)
   std::vector<int> blk, dims;
   std::vector<int64_t> roff;
   int64_t tot = 0, totw = 0;
   for (size_t i = 0; i < EL_.coarse.q.size(); ++i) {
     if (psi_off_[i] < 0) continue;
+    const int g = std::min(EL_.coarse.dim[i], ER_.coarse.dim[psi_rcoarse_[i]]);
     blk.push_back(int(i));
-    dims.push_back(EL_.coarse.dim[i]);
+    dims.push_back(g);
     roff.push_back(tot);
-    tot += int64_t(EL_.coarse.dim[i]) * EL_.coarse.dim[i];
-    totw += EL_.coarse.dim[i];
+    tot += int64_t(g) * g;
+    totw += g;
   }
   double* rho = static_cast<double*>(ex_->alloc(size_t(std::max<int64_t>(tot, 1)) * sizeof(double)));
   double* Z = static_cast<double*>(ex_->alloc(size_t(std::max<int64_t>(tot, 1)) * sizeof(double)));
@@ -158,7 +162,7 @@ std::vector<double> Engine::left_spectrum(const double* psi) {
   std::vector<GemmSeg> S;
   for (size_t k = 0; k < blk.size(); ++k) {
     const int i = blk[k];
-    const int cols = ER_.coarse.dim[psi_rcoarse_[i]];
+    const int rows = EL_.coarse.dim[i], cols = ER_.coarse.dim[psi_rcoarse_[i]];
     GemmProb q;
     q.C = rho + roff[k];
     q.ldc = dims[k];
@@ -167,7 +171,8 @@ std::vector<double> Engine::left_spectrum(const double* psi) {
     q.alpha = 1.0;
     q.accumulate = 0;
     q.s0 = int(S.size());
-    S.push_back(GemmSeg{psi + psi_off_[i], psi + psi_off_[i], cols, cols, cols, 0, 1});
+    if (rows <= cols) S.push_back(GemmSeg{psi + psi_off_[i], psi + psi_off_[i], cols, cols, cols, 0, 1});   // psi psi^T
+    else S.push_back(GemmSeg{psi + psi_off_[i], psi + psi_off_[i], cols, cols, rows, 1, 0});                // psi^T psi
     q.s1 = int(S.size());
     P.push_back(q);
   }
