@@ -58,6 +58,10 @@ def parse():
                     help="L,na,nb,D,n_sweeps: converge split-BF16 sweeps (D ramp from D/4), then time the adjoint "
                          "(dmrg_sigma_backward: one- and two-particle densities) and the orbital gradient at the "
                          "final state, checked by central differences of E(exp(kappa)) with h = 1e-5")
+    ap.add_argument("--mode-opt", default="",
+                    help="L,na,nb,D,n_macro: mode optimisation (Sec. 2.2) -- n_macro macro iterations, each one sweep "
+                         "with swap-gate layers and one sweep of micro-steps, after two plain sweeps; energies, "
+                         "entropies of the cuts and seconds, next to the same number of plain sweeps")
     ap.add_argument("--batched-davidson", type=int, default=0,
                     help="with --batched: for the first n problems, Davidson at the centre bond in FP64 and in "
                          "split-BF16 with refinement from the same start vector (per-problem |dE| and seconds)")
@@ -406,6 +410,8 @@ def main():
         extras.append(("sweep_compare", lambda: compare_sweeps(args, B, I, stream)))
     if args.differentiate:
         extras.append(("differentiation", lambda: differentiate(args, B, I, stream)))
+    if args.mode_opt:
+        extras.append(("mode_optimisation", lambda: mode_optimisation(args, B, I, stream)))
     for key, fn in extras:
         try:
             out[key] = fn()
@@ -604,6 +610,45 @@ def differentiate(args, B, I, stream):
             "orbital_gradient_norm": float(np.linalg.norm(GR)),
             "fd_checks_h1e-5": checks,
             "max_abs_diff_fd": max(c["abs_diff"] for c in checks)}
+
+
+def mode_optimisation(args, B, I, stream):
+    """Mode optimisation (Sec. 2.2): plain sweeps, then macro iterations of a sweep with swap-gate
+    layers and a sweep of micro-steps (rotation of least half-Renyi entropy at every left-to-right
+    step); the same total number of plain sweeps beside it."""
+    import torch
+    L, na, nb, D, nm = (int(x) for x in args.mode_opt.split(","))
+    t, v = I.synthetic_integrals(L, 7)
+    res = {"workload": f"L={L}, {na}a+{nb}b, D={D}, synthetic integrals seed 7: 2 plain sweeps, then {nm} macro "
+                       f"iteration(s) of one swap-layer sweep and one micro-step sweep (split-BF16, tol 1e-7)"}
+    dm = B.Dmrg(t, v, na, nb, D=D, seed=7, precision=B.PREC_MIXED_BF16, stream=stream.cuda_stream)
+    dp = B.Dmrg(t, v, na, nb, D=D, seed=7, precision=B.PREC_MIXED_BF16, stream=stream.cuda_stream)
+    e0 = list(dm.sweep(2, [D, D], tol=1e-7, check=False))
+    ep = list(dp.sweep(2, [D, D], tol=1e-7, check=False))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    macro = []
+    for k in range(nm):
+        es = dm.sweep(1, [D], tol=1e-7, check=False, swap_layers=True)
+        em = dm.sweep(1, [D], tol=1e-7, check=False, mode_opt=True)
+        lg = dm.mode_log()
+        macro.append({"energy_after_swaps": float(es[-1]), "energy_after_micro": float(em[-1]),
+                      "sum_S_half_before": float(sum(x["s_before"] for x in lg)),
+                      "sum_S_half_after": float(sum(x["s_after"] for x in lg)),
+                      "max_abs_theta": float(max(abs(x["theta"]) for x in lg))})
+    torch.cuda.synchronize()
+    t_mo = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ep += list(dp.sweep(2 * nm, [D] * (2 * nm), tol=1e-7, check=False))
+    torch.cuda.synchronize()
+    t_pl = time.perf_counter() - t0
+    res.update({"plain_energies": [float(x) for x in ep], "mode_opt_start": [float(x) for x in e0],
+                "macro_iterations": macro, "mode_opt_s": round(t_mo, 2), "plain_s": round(t_pl, 2),
+                "final_energy_mode_opt": macro[-1]["energy_after_micro"] if macro else None,
+                "final_energy_plain": float(ep[-1])})
+    dm.close()
+    dp.close()
+    return res
 
 
 def batched_bench(args, B, I):
