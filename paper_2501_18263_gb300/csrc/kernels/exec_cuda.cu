@@ -84,8 +84,9 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmTile* __restric
       }
       __syncthreads();
       if (busy) {
-#pragma unroll
-        for (int k = 0; k < TK; ++k) {
+        // a ragged K step (Kt < TK: the last one of a segment) runs only its own k
+#pragma unroll 4
+        for (int k = 0; k < Kt; ++k) {
           double a[4], b[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
