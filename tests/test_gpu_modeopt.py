@@ -66,10 +66,11 @@ def test_rotated_psi_matches_the_oracle_and_keeps_the_energy(case):
     d.close()
 
 
-def test_mode_step_lowers_the_entropy_and_keeps_the_energy():
+@pytest.mark.parametrize("order", [None, [2, 7, 0, 5, 1, 6, 3, 4]], ids=["chain", "permuted"])
+def test_mode_step_lowers_the_entropy_and_keeps_the_energy(order):
     L, na, nb, D = 8, 4, 4, 16
     t, v = I.synthetic_integrals(L, 150)
-    d = B.Dmrg(t, v, na, nb, D=D, seed=2, stream=stream())
+    d = B.Dmrg(t, v, na, nb, D=D, seed=2, order=order, stream=stream())
     d.sweep(1, [D], tol=1e-9, max_iter=400)
     bond, n = d.sweep_state()
     import torch
@@ -88,7 +89,14 @@ def test_mode_step_lowers_the_entropy_and_keeps_the_energy():
     e1 = d.expectation(bond, psi.data_ptr(), psi.data_ptr())
     assert abs(e1 - e0) <= 1e-10 * abs(e0)
     t2, v2 = d.get_integrals()
-    tr, vr = O.rotate_integrals(t, v, _pair(L, bond, theta))
+    # the rotation acts on the orbitals at chain positions bond, bond + 1: in the caller's
+    # numbering on orbitals order[bond], order[bond + 1]
+    o = np.arange(L) if order is None else np.asarray(order)
+    U = np.eye(L)
+    c, s_ = np.cos(theta), np.sin(theta)
+    p, q = o[bond], o[bond + 1]
+    U[p, p], U[p, q], U[q, p], U[q, q] = c, s_, -s_, c
+    tr, vr = O.rotate_integrals(t, v, U)
     np.testing.assert_allclose(t2, tr, atol=1e-13)
     np.testing.assert_allclose(v2, vr, atol=1e-13)
     d.close()

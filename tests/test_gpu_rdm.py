@@ -186,3 +186,25 @@ def test_autograd_energy_and_orbital_gradient_by_central_differences():
         fd = (es[0] - es[1]) / (2 * h)
         assert abs(fd - grad[p, q]) <= 1e-6 * max(1.0, abs(grad[p, q])), (p, q, fd, grad[p, q])
     d.close()
+
+
+def test_adjoint_under_a_small_memory_cap_equals_the_uncapped_one():
+    """The sigma-term intermediates of the adjoint are cut into chunks under mem_cap; the
+    densities do not depend on the cut (fixed-order accumulation over the chunks)."""
+    L, na, nb, D, bond = 10, 5, 4, 64, 4
+    t, v = I.synthetic_integrals(L, 91)
+    bp = I.bond_problem(L, na, nb, D, bond, seed=92)
+    out = []
+    for cap in (0, 1 << 20):
+        d = B.Dmrg(t, v, na, nb, D=D, mem_cap=cap, stream=stream())
+        d.load_bond_problem(bp)
+        d.prepare(bond)
+        psi = to_dev(B.pack_psi(bp.psi))
+        g1 = psi.new_zeros((L, L))
+        g2 = psi.new_zeros((L, L, L, L))
+        d.sigma_backward(bond, psi.data_ptr(), psi.data_ptr(), g1.data_ptr(), g2.data_ptr())
+        out.append((g1.cpu().numpy(), g2.cpu().numpy(), d.plan_paths()["chunks_fp64"]))
+        d.close()
+    assert out[1][2] > 1
+    assert np.max(np.abs(out[0][0] - out[1][0])) <= 1e-12 * np.max(np.abs(out[0][0]))
+    assert np.max(np.abs(out[0][1] - out[1][1])) <= 1e-12 * np.max(np.abs(out[0][1]))
