@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=1,
                     help="also time this many full two-site sweeps at bond dimension D (fresh seeded basis)")
     ap.add_argument("--sweep-tol", type=float, default=1e-6, help="Davidson residual tolerance of the timed sweeps")
+    ap.add_argument("--sweep-max-iter", type=int, default=100, help="Davidson iteration limit per sweep step")
     ap.add_argument("--refine-all", action="store_true",
                     help="split-BF16 sweeps: FP64 refinement at every step (not only the reported one)")
     ap.add_argument("--differentiate", default="",
@@ -418,7 +419,7 @@ def sweep_ramp(args, B, t, v, prec, stream):
     for D in Ds:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e = d.sweep(1, [D], tol=args.sweep_tol, refine_all=args.refine_all, check=False)
+        e = d.sweep(1, [D], tol=args.sweep_tol, refine_all=args.refine_all, check=False, max_iter=args.sweep_max_iter)
         torch.cuda.synchronize()
         res["sweeps"].append({"D": D, "seconds": round(time.perf_counter() - t0, 2), "energy": float(e[0]),
                               "phases_s": {k: round(x, 2) for k, x in d.sweep_phases().items()}})
@@ -506,7 +507,8 @@ def compare_sweeps(args, B, I, stream):
         per, e, lg, ph = [], [], [], {}
         for k in range(ns):   # one call per sweep: wall seconds of each
             t0 = time.perf_counter()
-            e += list(d.sweep(1, [Ds[k]], tol=args.sweep_tol, refine_all=args.refine_all, check=False))
+            e += list(d.sweep(1, [Ds[k]], tol=args.sweep_tol, refine_all=args.refine_all, check=False,
+                              max_iter=args.sweep_max_iter))
             torch.cuda.synchronize()
             per.append(round(time.perf_counter() - t0, 2))
             lg += d.sweep_log()
