@@ -52,6 +52,8 @@ def parse():
                     help="also time this many full two-site sweeps at bond dimension D (fresh seeded basis)")
     ap.add_argument("--sweep-tol", type=float, default=1e-6, help="Davidson residual tolerance of the timed sweeps")
     ap.add_argument("--sweep-max-iter", type=int, default=100, help="Davidson iteration limit per sweep step")
+    ap.add_argument("--mem-cap-gb", type=float, default=0.0,
+                    help="mem_cap_bytes of the sweep handles (chunks the per-term intermediates; 0 = library default)")
     ap.add_argument("--refine-all", action="store_true",
                     help="split-BF16 sweeps: FP64 refinement at every step (not only the reported one)")
     ap.add_argument("--differentiate", default="",
@@ -413,9 +415,11 @@ def sweep_ramp(args, B, t, v, prec, stream):
     Sec. 4.1 phase split and energy of each sweep."""
     import torch
     Ds = [int(x) for x in args.sweep_ramp.split(",")]
-    d = B.Dmrg(t, v, args.na, args.nb, D=Ds[0], precision=prec, seed=args.seed, stream=stream.cuda_stream)
+    d = B.Dmrg(t, v, args.na, args.nb, D=Ds[0], precision=prec, seed=args.seed, stream=stream.cuda_stream,
+               mem_cap=int(args.mem_cap_gb * 2 ** 30))
     res = {"workload": f"one full sweep L->R->L per D in {Ds} on one handle, L={args.L}, {args.na}a+{args.nb}b, "
-                       f"from the seeded product-state basis, Davidson tol {args.sweep_tol:g}", "sweeps": []}
+                       f"from the seeded product-state basis, Davidson tol {args.sweep_tol:g}"
+                       + (f", mem_cap {args.mem_cap_gb:g} GB" if args.mem_cap_gb else ""), "sweeps": []}
     for D in Ds:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
