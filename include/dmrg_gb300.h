@@ -245,6 +245,11 @@ dmrg_status dmrg_set_integrals(dmrg_handle* h, const double* t, const double* v)
  * (may be NULL to query the size). */
 dmrg_status dmrg_sweep_state(dmrg_handle* h, int32_t* bond, int64_t* psi_size, double* psi_dev);
 
+/* Make psi (device, in the layout of the prepared `bond`) the handle's current
+ * state: dmrg_sweep_state returns it, dmrg_mode_step rotates it, and a following
+ * dmrg_sweep starts from it when `bond` is 0.  The library keeps its own copy. */
+dmrg_status dmrg_set_state(dmrg_handle* h, int32_t bond, const double* psi_dev);
+
 /* <lam| H_eff |psi> at `bond` with the FP64 sigma (device vectors; *value on
  * the host). */
 dmrg_status dmrg_expectation(dmrg_handle* h, int32_t bond, const double* lam_dev, const double* psi_dev,

@@ -19,7 +19,7 @@ PREC_FP64, PREC_MIXED_BF16 = 0, 1
 
 SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "dmrg_sigma",
            "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_ex", "dmrg_sweep_log", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_set_integrals",
-           "dmrg_sweep_state", "dmrg_expectation", "dmrg_orbital_gradient", "dmrg_term_work",
+           "dmrg_sweep_state", "dmrg_set_state", "dmrg_expectation", "dmrg_orbital_gradient", "dmrg_term_work",
            "dmrg_term_partition", "dmrg_sigma_subset", "dmrg_graph_replays", "dmrg_two_site_rotate",
            "dmrg_half_renyi", "dmrg_mode_step", "dmrg_get_integrals", "dmrg_mode_log", "dmrg_stats",
            "dmrg_plan_paths", "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
@@ -70,6 +70,7 @@ def load_library(path: str | None = None):
         "dmrg_sigma_backward": ([vp, i32, vp, vp, vp, vp], ctypes.c_int),
         "dmrg_set_integrals": ([vp, dp, dp], ctypes.c_int),
         "dmrg_sweep_state": ([vp, ip, i64p, vp], ctypes.c_int),
+        "dmrg_set_state": ([vp, i32, vp], ctypes.c_int),
         "dmrg_expectation": ([vp, i32, vp, vp, dp], ctypes.c_int),
         "dmrg_orbital_gradient": ([vp, vp, vp, vp], ctypes.c_int),
         "dmrg_term_work": ([vp, i32, ip, i64p], ctypes.c_int),
@@ -250,6 +251,9 @@ class Dmrg:
         self._check(self.lib.dmrg_sweep_state(self.h, ctypes.byref(b), ctypes.byref(n),
                                               ctypes.c_void_p(int(psi_ptr)) if psi_ptr else None))
         return b.value, n.value
+
+    def set_state(self, bond, psi_ptr):
+        self._check(self.lib.dmrg_set_state(self.h, bond, ctypes.c_void_p(int(psi_ptr))))
 
     def expectation(self, bond, lam_ptr, psi_ptr):
         out = ctypes.c_double()

@@ -391,6 +391,15 @@ dmrg_status dmrg_sweep_state(dmrg_handle* h, int32_t* bond, int64_t* psi_size, d
   });
 }
 
+dmrg_status dmrg_set_state(dmrg_handle* h, int32_t bond, const double* psi) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !psi) return fail(DMRG_ERR_ARG, "null argument");
+    if (h->eng->bond() != bond) return fail(DMRG_ERR_ARG, "bond not prepared (call dmrg_prepare)");
+    h->eng->set_state(psi);
+    return DMRG_OK;
+  });
+}
+
 dmrg_status dmrg_expectation(dmrg_handle* h, int32_t bond, const double* lam, const double* psi, double* value) {
   return guard([&]() -> dmrg_status {
     if (!h || !lam || !psi || !value) return fail(DMRG_ERR_ARG, "null argument");

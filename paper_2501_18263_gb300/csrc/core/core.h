@@ -239,6 +239,8 @@ class Engine {
   void set_integrals(const std::vector<double>& t, const std::vector<double>& v);
   // wave function of the last sweep (device, at bond(); nullptr before a sweep)
   const double* sweep_psi() const { return psi_cur_; }
+  // make psi (device, psi_size of the prepared bond) the current state
+  void set_state(const double* psi);
 
   // mode optimisation (Sec. 2.2, Fig. 1; modeopt.cpp): psi in the orbitals rotated
   // by theta at the two sites of the prepared bond; the half-Renyi entropy of the
@@ -249,7 +251,8 @@ class Engine {
   double half_renyi(const double* psi);
   double entropy_at(double theta, const double* psi, double* scratch);
   double best_rotation(const double* psi, double* s_min, double* s0);
-  void rotate_integrals_pair(int k, double theta);
+  void rotate_integrals_pair(int k, double theta, bool rebuild);
+  void rotate_block_ops(int k, double theta);
   double mode_step(double* s_before, double* s_after);
   void apply_rotation(double theta);   // rotate the swept state and the integrals at bond()
   const std::vector<double>& chain_t() const { return P_.t; }

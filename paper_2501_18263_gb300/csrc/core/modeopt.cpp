@@ -252,7 +252,7 @@ double Engine::best_rotation(const double* psi, double* s_min, double* s0_out) {
   return best;
 }
 
-void Engine::rotate_integrals_pair(int k, double theta) {
+void Engine::rotate_integrals_pair(int k, double theta, bool rebuild) {
   const int L = P_.L;
   const double c = std::cos(theta), s = std::sin(theta);
   // U = identity except U[k][k] = c, U[k][k+1] = s, U[k+1][k] = -s, U[k+1][k+1] = c
@@ -298,7 +298,127 @@ void Engine::rotate_integrals_pair(int k, double theta) {
     }
     cur = nx;
   }
-  set_integrals(t2, cur);
+  if (rebuild) {
+    set_integrals(t2, cur);
+  } else {
+    P_.t = t2;
+    P_.v = cur;
+  }
+}
+
+// The stored block operators after the rotation of the orbitals at chain positions
+// k, k+1 (both explicit at bond k).  No block holds those orbitals inside it; they
+// enter only as the external indices of complementary operators, each of which is
+// linear in every external index:  S_q on left blocks,  T_p, P_pr, Q_pq on right
+// blocks.  So  O'_{x..} = sum_y U_xy O_{y..}  per rotated index (U acting on the
+// spatial orbital, spin kept), with P_rp = -P_pr, P_pp = 0 and Q_qp = Q_pq^T for the
+// orders that are not stored.  Left blocks B_1..B_k and right blocks C_{k+2}..C_{L-1}
+// are updated (the ones the sweep uses before it rebuilds them).
+void Engine::rotate_block_ops(int k, double theta) {
+  const double c = std::cos(theta), s = std::sin(theta);
+  // row x of U on spin-orbitals: (y, U_xy)
+  auto urow = [&](int x) {
+    std::vector<std::pair<int, double>> r;
+    const int site = x >> 1, sg = x & 1;
+    if (site == k) {
+      r.push_back({x, c});
+      r.push_back({2 * (k + 1) + sg, s});
+    } else if (site == k + 1) {
+      r.push_back({2 * k + sg, -s});
+      r.push_back({x, c});
+    } else {
+      r.push_back({x, 1.0});
+    }
+    return r;
+  };
+  auto rotated = [&](int x) { return (x >> 1) == k || (x >> 1) == k + 1; };
+  struct Src { OpKey key; int trans; double coef; };
+  auto update = [&](Block& B, bool left) {
+    if (!B.valid || B.ops.n_elem == 0) return;
+    OpSet& os = B.ops;
+    std::vector<std::pair<OpKey, std::vector<Src>>> work;
+    for (auto& kv : os.ops) {
+      const OpKey& key = kv.first;
+      std::vector<Src> src;
+      if (left) {
+        if (key.type != OP_S || !rotated(key.i)) continue;
+        for (auto& y : urow(key.i)) src.push_back(Src{OpKey{OP_S, y.first, 0}, 0, y.second});
+      } else if (key.type == OP_T) {
+        if (!rotated(key.i)) continue;
+        for (auto& y : urow(key.i)) src.push_back(Src{OpKey{OP_T, y.first, 0}, 0, y.second});
+      } else if (key.type == OP_P) {
+        if (!rotated(key.i) && !rotated(key.j)) continue;
+        for (auto& y1 : urow(key.i))
+          for (auto& y2 : urow(key.j)) {
+            if (y1.first == y2.first) continue;
+            const double u = y1.second * y2.second;
+            if (y1.first < y2.first) src.push_back(Src{OpKey{OP_P, y1.first, y2.first}, 0, u});
+            else src.push_back(Src{OpKey{OP_P, y2.first, y1.first}, 0, -u});
+          }
+      } else if (key.type == OP_Q) {
+        if (!rotated(key.i) && !rotated(key.j)) continue;
+        for (auto& y1 : urow(key.i))
+          for (auto& y2 : urow(key.j)) {
+            const double u = y1.second * y2.second;
+            if (y1.first <= y2.first) src.push_back(Src{OpKey{OP_Q, y1.first, y2.first}, 0, u});
+            else src.push_back(Src{OpKey{OP_Q, y2.first, y1.first}, 1, u});
+          }
+      } else {
+        continue;
+      }
+      work.push_back({key, src});
+    }
+    if (work.empty()) return;
+    double* scratch = static_cast<double*>(ex_->alloc(size_t(os.n_elem) * sizeof(double)));
+    std::vector<KronGroup> g;
+    std::vector<KronTask> tk;
+    for (auto& w : work) {
+      const Op& tgt = os.ops.at(w.first);
+      for (const OpBlk& tb : tgt.blk) {
+        KronGroup kg;
+        kg.dst = scratch + tb.off;
+        kg.ld = tb.cols;
+        kg.rows = tb.rows;
+        kg.cols = tb.cols;
+        kg.accumulate = 0;
+        kg.t0 = int(tk.size());
+        for (const Src& sr : w.second) {
+          auto it = os.ops.find(sr.key);
+          if (it == os.ops.end()) continue;
+          const Op& so = it->second;
+          // block (tb.r <- tb.c) of the source, or of its transpose
+          const int want_c = sr.trans ? tb.r : tb.c, want_r = sr.trans ? tb.c : tb.r;
+          auto bc = so.by_col.find(want_c);
+          if (bc == so.by_col.end()) continue;
+          const OpBlk& sb = so.blk[bc->second];
+          if (sb.r != want_r) continue;
+          tk.push_back(KronTask{os.arena + sb.off, sb.cols, sr.trans, sr.coef});
+        }
+        kg.t1 = int(tk.size());
+        g.push_back(kg);
+      }
+    }
+    if (!g.empty()) ex_->kron(g, tk);
+    for (auto& w : work) {
+      const Op& tgt = os.ops.at(w.first);
+      for (const OpBlk& tb : tgt.blk)
+        ex_->d2d(os.arena + tb.off, scratch + tb.off, size_t(tb.rows) * tb.cols * sizeof(double));
+    }
+    ex_->release(scratch);
+  };
+  for (int n = 1; n <= k; ++n) update(lb_[n], true);
+  for (int m = k + 2; m < P_.L; ++m) update(rb_[m], false);
+}
+
+void Engine::set_state(const double* psi) {
+  if (bond_ < 0) throw std::runtime_error("set_state: no bond prepared");
+  if (!psi_cur_ || psi_cur_cap_ < psi_n_) {
+    if (psi_cur_) ex_->release(psi_cur_);
+    psi_cur_ = static_cast<double*>(ex_->alloc(size_t(psi_n_) * sizeof(double)));
+  }
+  psi_cur_cap_ = psi_n_;
+  ex_->d2d(psi_cur_, psi, size_t(psi_n_) * sizeof(double));
+  ex_->sync();
 }
 
 void Engine::apply_rotation(double theta) {
@@ -309,9 +429,10 @@ void Engine::apply_rotation(double theta) {
   rotate_two_site(theta, psi_cur_, tmp);
   ex_->d2d(psi_cur_, tmp, size_t(psi_n_) * sizeof(double));
   ex_->release(tmp);
-  rotate_integrals_pair(b, theta);
-  build_left_blocks(b);
-  build_right_blocks(b + 2);
+  // new integrals, the stored block operators rotated in place, the enlarged
+  // operators and plans of the bond rebuilt
+  rotate_integrals_pair(b, theta, false);
+  rotate_block_ops(b, theta);
   prepare_bond(b);
 }
 

@@ -150,3 +150,32 @@ def test_swap_layers_permute_the_modes_and_bring_every_pair_together():
     np.testing.assert_allclose(v2, vr, atol=1e-13)
     assert len(cover) == L * (L - 1) // 2
     d.close()
+
+
+@pytest.mark.parametrize("bond", [0, 3, 6], ids=["bond0", "bond3", "bond6"])
+def test_in_place_rotation_of_the_block_operators_equals_a_rebuild(bond):
+    """The micro-step rotates the stored complementary operators in place (each is linear in
+    its external indices: S_q of the left blocks, T_p, P_pr, Q_pq of the right ones);
+    rebuilding every block from the same isometries and the rotated integrals must give the
+    same sigma, at the chain ends and inside."""
+    L, na, nb, D = 8, 4, 3, 24
+    t, v = I.synthetic_integrals(L, 180)
+    bp = I.bond_problem(L, na, nb, D, bond, seed=181)
+    d = B.Dmrg(t, v, na, nb, D=D, stream=stream())
+    d.load_bond_problem(bp)
+    d.prepare(bond)
+    psi = to_dev(B.pack_psi(bp.psi))
+    d.set_state(bond, psi.data_ptr())
+    for _ in range(2):                       # two micro-steps: rotations compose
+        theta, s0, s1 = d.mode_step()
+    d.sweep_state(psi.data_ptr())
+    s_in = psi.new_empty(psi.shape)
+    d.sigma(bond, psi.data_ptr(), s_in.data_ptr())
+    t2, v2 = d.get_integrals()
+    d.set_integrals(t2, v2)
+    d.prepare(bond)
+    s_re = psi.new_empty(psi.shape)
+    d.sigma(bond, psi.data_ptr(), s_re.data_ptr())
+    a, b = s_in.cpu().numpy(), s_re.cpu().numpy()
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+    d.close()
