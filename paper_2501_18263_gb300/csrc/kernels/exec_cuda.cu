@@ -880,6 +880,7 @@ class CudaExec : public Exec {
     int64_t* bcol = nullptr;
     int64_t* ccol = nullptr;
     float* acol = nullptr;
+    int* next_tile = nullptr;
     int ntiles = 0;
     int cls = PROF_MIXED;
     bool live = false;
@@ -964,6 +965,7 @@ class CudaExec : public Exec {
     pl.bcol = upload(bcol);
     pl.ccol = upload(ccol);
     pl.acol = upload(acol);
+    pl.next_tile = static_cast<int*>(alloc(sizeof(int)));
     pl.live = true;
     pl.cls = (!p.empty() && p[0].mode != 0) ? PROF_MIXED1 : PROF_MIXED;
     pl.host = MixPlanHost{p, s, bcol, ccol, acol};
@@ -978,7 +980,12 @@ class CudaExec : public Exec {
   void mix_run(int id) override {
     MixPlanD& pl = mplans_.at(id);
     if (!pl.ntiles) return;
-    launch(pl.cls, [&] { launch_mixed_gemm(pl.tiles, pl.ntiles, pl.probs, pl.segs, pl.bcol, pl.ccol, pl.acol, err_, nsm_, st_); });
+    launch(pl.cls, [&] {
+      // tiles handed out through the counter where they are long (the K-concatenated
+      // products of stage 2); in fixed strides where they are short (stage 1)
+      int* nt = pl.cls == PROF_MIXED ? pl.next_tile : nullptr;
+      launch_mixed_gemm(pl.tiles, pl.ntiles, pl.probs, pl.segs, pl.bcol, pl.ccol, pl.acol, err_, nt, nsm_, st_);
+    });
   }
   void mix_plan_free(int id) override { mix_free(id); }
   const MixPlanHost& mix_plan_host(int id) const override { return mplans_.at(id).host; }
@@ -1012,6 +1019,7 @@ class CudaExec : public Exec {
     cudaFreeAsync(pl.bcol, st_);
     cudaFreeAsync(pl.ccol, st_);
     cudaFreeAsync(pl.acol, st_);
+    cudaFreeAsync(pl.next_tile, st_);
     pl.host = MixPlanHost{};
     pl.live = false;
   }

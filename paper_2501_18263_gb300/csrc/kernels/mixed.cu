@@ -250,7 +250,8 @@ __device__ __forceinline__ void tmem_st2x8(uint32_t t0, uint32_t t1, const float
 __global__ void __maxnreg__(96)
     mixed_gemm_kernel(const MixTile* __restrict__ tiles, int ntiles, const MixProb* __restrict__ probs,
                       const MixSeg* __restrict__ segs, const int64_t* __restrict__ bcol,
-                      const int64_t* __restrict__ ccol, const float* __restrict__ acol, int* err) {
+                      const int64_t* __restrict__ ccol, const float* __restrict__ acol, int* err,
+                      int* next_tile) {
   extern __shared__ __align__(1024) uint8_t smem[];
   TileSlot* slots = reinterpret_cast<TileSlot*>(smem + SLOT_OFF);
   StageInfo* info = reinterpret_cast<StageInfo*>(smem + INFO_OFF);
@@ -357,25 +358,34 @@ __global__ void __maxnreg__(96)
     // and two tiles ahead.
     int step = 0, tcount = 0;
     bool stop = false;
-    const int t0 = blockIdx.x;
-    MixTile t1{}, t2{};
+    // CTA c starts with tile c.  With a counter (next_tile), each next tile is
+    // claimed from it when the CTA starts the previous one, so tiles are handed out
+    // in list order: tiles next to each other in the list share operand slabs (the
+    // tiles of one output block) and start within a tile's claim of each other,
+    // reading the shared slabs while the L2 still holds them.  Without one, CTA c
+    // takes tiles c, c + G, c + 2G, ... (no atomic on the path of short tiles).
+    int ti = blockIdx.x;
+    MixTile t1{};
     MixProb p1{};
     MixSeg g1{};
-    if (t0 < ntiles) {
-      t1 = tiles[t0];
+    if (ti < ntiles) {
+      t1 = tiles[ti];
       p1 = probs[t1.prob];
       if (p1.s1 > p1.s0) g1 = segs[p1.s0];
     }
-    if (t0 + G < ntiles) t2 = tiles[t0 + G];
-    for (int ti = t0; ti < ntiles && !stop; ti += G, ++tcount) {
+    for (; ti < ntiles && !stop; ++tcount) {
       const MixTile tl = t1;
       const MixProb p = p1;
       const MixSeg gf = g1;
-      if (ti + G < ntiles) {
-        t1 = t2;
+      int nx = ti + G;
+      if (next_tile) {
+        if (lane == 0) nx = G + atomicAdd(next_tile, 1);
+        nx = __shfl_sync(0xffffffffu, nx, 0);
+      }
+      if (nx < ntiles) {
+        t1 = tiles[nx];
         p1 = probs[t1.prob];
         if (p1.s1 > p1.s0) g1 = segs[p1.s0];
-        if (ti + 2 * G < ntiles) t2 = tiles[ti + 2 * G];
       }
       const int slot = tcount & 1;
       if (tcount >= 2 && !mbar_wait_warp(slot_empty(slot), ((tcount >> 1) - 1) & 1, abort_flag, err, 6)) {
@@ -398,6 +408,7 @@ __global__ void __maxnreg__(96)
         sl.row0 = p.row0;
         sl.crows = p.crows;
         sl.alpha = p.alpha;
+        sl.pad = 0;   // a tile (1 marks the sentinel)
         if (p.mode == 3) {
           const int Mt = min(MIX_TM, p.M - tl.m0);
           mbar_expect_tx(slot_full(slot), uint32_t(Mt) * 12u);
@@ -439,6 +450,20 @@ __global__ void __maxnreg__(96)
           }
         }
       }
+      ti = nx;
+    }
+    if (!stop) {
+      // sentinel tile slot: the drain warps stop at it
+      const int slot = tcount & 1;
+      if (tcount >= 2 && !mbar_wait_warp(slot_empty(slot), ((tcount >> 1) - 1) & 1, abort_flag, err, 6)) {
+        stop = true;
+      } else {
+        if (lane == 0) {
+          slots[slot].pad = 1;
+          mbar_arrive(slot_full(slot));
+        }
+        ++tcount;
+      }
     }
     if (!stop) {
       // end marker for the MMA issuer
@@ -467,10 +492,11 @@ __global__ void __maxnreg__(96)
     const int row = (warp & 3) * 32 + lane;      // TMEM lane quarter = warp % 4
     const uint32_t tq = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + uint32_t(DRAIN_COLS * ch);
     int chunk = 0, tcount = 0;
-    for (int ti = blockIdx.x; ti < ntiles; ti += G, ++tcount) {
+    for (;; ++tcount) {
       const int slot = tcount & 1;
       if (!mbar_wait_warp(slot_full(slot), (tcount >> 1) & 1, abort_flag, err, 7)) break;
       const TileSlot& S = slots[slot];
+      if (S.pad) break;   // the sentinel: no more tiles for this CTA
       const int nch = S.nch;
       const bool mine = DRAIN_COLS * ch < S.Nt;  // this warp's columns exist in the tile
       // running sum per element: sh + sl, where sh collects the hi x hi chunks
@@ -675,15 +701,18 @@ __global__ void df_to_f64_kernel(const float* __restrict__ hi, const float* __re
 }  // namespace
 
 void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, const MixSeg* segs,
-                       const int64_t* bcol, const int64_t* ccol, const float* acol, int* err, int nsm,
-                       cudaStream_t st) {
+                       const int64_t* bcol, const int64_t* ccol, const float* acol, int* err, int* next_tile,
+                       int nsm, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(mixed_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     attr = true;
   }
   const int grid = ntiles < nsm ? ntiles : nsm;
-  if (ntiles > 0) mixed_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(tiles, ntiles, probs, segs, bcol, ccol, acol, err);
+  if (ntiles > 0) {
+    if (next_tile) cudaMemsetAsync(next_tile, 0, sizeof(int), st);
+    mixed_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(tiles, ntiles, probs, segs, bcol, ccol, acol, err, next_tile);
+  }
 }
 
 void launch_split(const SplitTask* t, int ntask, cudaStream_t st) {

@@ -14,10 +14,12 @@ struct MixTile {
 };
 
 // launch the grouped split-BF16 GEMM over `ntiles` tiles; err is a device int
-// that receives a nonzero code when a bounded wait gives up
+// that receives a nonzero code when a bounded wait gives up; next_tile, when not
+// null, is a device int through which the launch hands out tiles in list order
+// (cleared by the launch; one per plan), else CTAs take tiles in fixed strides
 void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, const MixSeg* segs,
-                       const int64_t* bcol, const int64_t* ccol, const float* acol, int* err, int nsm,
-                       cudaStream_t st);
+                       const int64_t* bcol, const int64_t* ccol, const float* acol, int* err, int* next_tile,
+                       int nsm, cudaStream_t st);
 void launch_split(const SplitTask* t, int ntask, cudaStream_t st);
 void launch_reduce_parts(const float* part, int nparts, int64_t n, float* hi, float* lo, int accumulate, int grid,
                          cudaStream_t st);
