@@ -299,6 +299,23 @@ dmrg_status dmrg_sigma_subset(dmrg_handle* h, int32_t bond, const double* psi_de
 dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out16);
 
 /*
+ * The eigensolver of the truncation step (Sec. 2.1: the kept states of a block are
+ * the leading eigenvectors of its reduced density matrix, sector by sector), on
+ * caller data: nmat dense symmetric FP64 matrices, matrix b of order n[b] (host
+ * array, every n[b] >= 1), packed one after the other in device memory, row-major:
+ * A holds sum_b n[b]^2 doubles (destroyed), Z receives the eigenvectors as columns
+ * (same layout, a separate buffer), w receives the eigenvalues of each matrix in
+ * ascending order (sum_b n[b] doubles).  Householder tridiagonalisation and
+ * implicit QL in FP64, the kernels the truncation step runs.  rot_cap bounds the
+ * rotations recorded per matrix before they are applied (0: n[b]^2; smaller values
+ * use less scratch memory and more passes).  Returns DMRG_ERR_NOCONV when a QL
+ * iteration does not converge (results undefined), DMRG_ERR_ARG on bad arguments.
+ * Runs on the handle's stream and device; synchronous.
+ */
+dmrg_status dmrg_eigh_batch(dmrg_handle* h, int32_t nmat, const int32_t* n, double* A_dev, double* w_dev,
+                            double* Z_dev, int32_t rot_cap);
+
+/*
  * Mode optimisation (Sec. 2.2, Fig. 1).  A spin-independent rotation of the two
  * orbitals at the sites k, k+1 of a bond by the angle theta: the new orbitals are
  *   c~+_k = cos(theta) c+_k + sin(theta) c+_{k+1},  c~+_{k+1} = -sin(theta) c+_k + cos(theta) c+_{k+1}

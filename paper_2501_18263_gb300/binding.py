@@ -21,7 +21,7 @@ SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "d
            "dmrg_sigma_ex", "dmrg_sigma_host", "dmrg_sigma_host_noalloc", "dmrg_davidson", "dmrg_sweep", "dmrg_sweep_ex", "dmrg_sweep_log", "dmrg_sweep_phases", "dmrg_sigma_backward", "dmrg_set_integrals",
            "dmrg_sweep_state", "dmrg_set_state", "dmrg_expectation", "dmrg_orbital_gradient", "dmrg_term_work",
            "dmrg_term_partition", "dmrg_sigma_subset", "dmrg_graph_replays", "dmrg_two_site_rotate",
-           "dmrg_half_renyi", "dmrg_mode_step", "dmrg_get_integrals", "dmrg_mode_log", "dmrg_stats",
+           "dmrg_half_renyi", "dmrg_eigh_batch", "dmrg_mode_step", "dmrg_get_integrals", "dmrg_mode_log", "dmrg_stats",
            "dmrg_plan_paths", "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
            "dmrg_last_error"]
 SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
@@ -79,6 +79,7 @@ def load_library(path: str | None = None):
         "dmrg_graph_replays": ([vp, i64p], ctypes.c_int),
         "dmrg_two_site_rotate": ([vp, i32, f64, vp, vp], ctypes.c_int),
         "dmrg_half_renyi": ([vp, i32, vp, dp], ctypes.c_int),
+        "dmrg_eigh_batch": ([vp, i32, ip, vp, vp, vp, i32], ctypes.c_int),
         "dmrg_mode_step": ([vp, dp, dp, dp], ctypes.c_int),
         "dmrg_get_integrals": ([vp, dp, dp], ctypes.c_int),
         "dmrg_mode_log": ([vp, ip, ctypes.POINTER(dp)], ctypes.c_int),
@@ -285,6 +286,12 @@ class Dmrg:
         x = ctypes.c_double()
         self._check(self.lib.dmrg_half_renyi(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.byref(x)))
         return x.value
+
+    def eigh_batch(self, n, A_ptr, w_ptr, Z_ptr, rot_cap=0):
+        """eigen-decomposition of packed symmetric matrices (device pointers; A destroyed)"""
+        nn = np.ascontiguousarray(n, dtype=np.int32)
+        self._check(self.lib.dmrg_eigh_batch(self.h, len(nn), nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.c_void_p(int(A_ptr)),
+                                             ctypes.c_void_p(int(w_ptr)), ctypes.c_void_p(int(Z_ptr)), int(rot_cap)))
 
     def mode_step(self):
         th, s0, s1 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -435,6 +435,31 @@ dmrg_status dmrg_orbital_gradient(dmrg_handle* h, const double* g1, const double
   });
 }
 
+dmrg_status dmrg_eigh_batch(dmrg_handle* h, int32_t nmat, const int32_t* n, double* A, double* w, double* Z,
+                            int32_t rot_cap) {
+  return guard([&]() -> dmrg_status {
+    if (!h || !n || !A || !w || !Z) return fail(DMRG_ERR_ARG, "null argument");
+    if (nmat <= 0) return fail(DMRG_ERR_ARG, "nmat must be positive");
+    if (A == Z) return fail(DMRG_ERR_ARG, "A and Z must be different buffers");
+    if (rot_cap < 0) return fail(DMRG_ERR_ARG, "rot_cap must be >= 0");
+    std::vector<double*> Av, wv, Zv;
+    std::vector<int> nv;
+    int64_t ao = 0, wo = 0;
+    for (int32_t b = 0; b < nmat; ++b) {
+      if (n[b] <= 0 || n[b] > 6000) return fail(DMRG_ERR_ARG, "matrix order out of range (1..6000)");
+      Av.push_back(A + ao);
+      Zv.push_back(Z + ao);
+      wv.push_back(w + wo);
+      nv.push_back(n[b]);
+      ao += int64_t(n[b]) * n[b];
+      wo += n[b];
+    }
+    h->eng->exec()->syev(Av, wv, Zv, nv, rot_cap);
+    h->eng->exec()->sync();
+    return check_device(h);
+  });
+}
+
 dmrg_status dmrg_two_site_rotate(dmrg_handle* h, int32_t bond, double theta, const double* psi, double* out) {
   return guard([&]() -> dmrg_status {
     if (!h || !psi || !out) return fail(DMRG_ERR_ARG, "null argument");

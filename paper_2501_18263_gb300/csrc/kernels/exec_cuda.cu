@@ -4,7 +4,9 @@
 //   mdot/lincomb  Davidson Gram-Schmidt and Ritz vectors (deterministic reductions)
 //   ritz          cyclic Jacobi eigensolver of the small Rayleigh-Ritz matrix
 //   syev          Householder tridiagonalisation + implicit QL eigensolver of the
-//                 density matrices of the truncation (one CTA per sector block)
+//                 density matrices of the truncation (reduction one CTA per sector
+//                 block; QL recurrence one thread per block, its rotations applied
+//                 by a warp per 32 rows)
 // All work is ordered on one stream; allocations are stream-ordered.
 #include <cuda_runtime.h>
 
@@ -390,15 +392,49 @@ __device__ void jacobi_core(double* A, double* Z, int n, int ld, double* cs, int
   }
 }
 
-// batched eigen-decomposition, one CTA per matrix (matrices in global memory)
+// Batched symmetric eigen-decomposition A = Z diag(w) Z^T (FP64), the classical
+// route split into phases, so that only the inherently sequential recurrence runs
+// on one thread and the O(n^3) phases other than the reduction spread over the GPU:
+//  1. Householder reduction to tridiagonal form, A = Q T Q^T with
+//     Q = H_0 ... H_{n-3}, H_k = I - tau_k u_k u_k^T (u_k supported on k+1..n-1),
+//     one CTA per small matrix, a cluster of eight per large one (syev_tridiag_kernel);
+//  2. Q formed explicitly, one warp per column: column j of Q is e_j with the
+//     reflectors k < j applied in the order k = j-1, ..., 0 (the reflectors k >= j
+//     leave e_j alone) (syev_qform_kernel);
+//  3. implicit QL iterations with shifts on T (Bowdler, Martin, Reinsch and
+//     Wilkinson, "The QR and QL algorithms for symmetric matrices", Numer. Math.
+//     11 (1968), the tql2 procedure): the scalar recurrences of one matrix on one
+//     thread, which records each iteration's plane rotations instead of applying
+//     them (syev_ql_kernel);
+//  4. the recorded rotations applied to Z = Q: a column rotation acts on every row
+//     alone, so each thread takes one row through all rotations in order, one warp
+//     per 32 rows (syev_rot_kernel);
+//  5. eigenvalues sorted ascending, eigenvectors permuted with them
+//     (syev_sort_kernel, syev_perm_kernel).
+// A dependent FP64 operation takes tens of cycles on this GPU (a square root or a
+// division hundreds), so the recurrence of step 3 takes one reciprocal square root
+// per rotation: with q = f^2 + g^2 and t = rsqrt(q), r = q t, c = g t, s = f t
+// (hypot and a division where q would under- or overflow), and it keeps the
+// diagonal and off-diagonal entries it walks over in registers.
 struct SyevJob {
-  double* A;
-  double* w;
-  double* Z;
-  int n, pad;
+  double* A;      // n x n input, destroyed
+  double* w;      // out: n eigenvalues, ascending
+  double* Z;      // out: n x n eigenvectors as columns (row-major, ld n)
+  double* d;      // n: diagonal of T, then the (unsorted) eigenvalues
+  double* e;      // n: off-diagonal of T (e[i] couples i and i + 1)
+  double* tau;    // n: reflector scalars
+  double* Zc;     // n x n working copy of Z, column-major: Zc[c * n + r]
+  double* U;      // n x n: reflector k in row k (u_k[k + 1] = 1)
+  double* pb;     // n: p = tau A22 v exchanged between the CTAs of a cluster
+  double2* rot;   // recorded rotations (c, s), capacity rcap
+  int4* hdr;      // per QL iteration: (first column i0, count, offset in rot, 0), capacity hcap
+  int* perm;      // n: sorted position of eigenvalue i
+  int* nh;        // headers left for syev_rot_kernel
+  int n, rcap, hcap, pad;
 };
 
 constexpr int SYEV_THREADS = 1024;
+constexpr int SYEV_CLUSTER = 8;   // CTAs per large matrix in the reduction (portable cluster size)
 
 // sum over the CTA, returned to every thread (red: >= 33 doubles of shared memory)
 __device__ double block_sum(double v, double* red) {
@@ -416,80 +452,95 @@ __device__ double block_sum(double v, double* red) {
   return red[32];
 }
 
-// Symmetric eigen-decomposition A = Z diag(w) Z^T (FP64), the classical route:
-//  1. Householder reduction to tridiagonal form, A = Q T Q^T with
-//     Q = H_0 ... H_{n-3}, H_k = I - tau_k u_k u_k^T (u_k supported on k+1..n-1);
-//  2. Q formed explicitly from the reflectors (backward accumulation);
-//  3. implicit QL iterations with shifts on T (Bowdler, Martin, Reinsch and
-//     Wilkinson, "The QR and QL algorithms for symmetric matrices", Numer. Math.
-//     11 (1968), the tql2 procedure), the plane rotations of every iteration
-//     applied to the columns of Z = Q;
-//  4. eigenvalues sorted ascending, eigenvectors permuted with them.
-// One thread runs the scalar QL recurrences; all threads apply each iteration's
-// rotations to their rows of Z (Z kept column-major while working, so that a
-// rotation of two columns is a coalesced pass).  On non-convergence (more than 60
-// QL iterations for one eigenvalue) *err receives 9.
-__global__ void __launch_bounds__(SYEV_THREADS) syev_kernel(const SyevJob* jobs, int* err, double* work_d,
-                                                           int maxn) {
-  const SyevJob jb = jobs[blockIdx.x];
+// index j of the segment holding x, given prefix sums pre[0..nj] (pre[0] = 0)
+__device__ __forceinline__ int syev_find(const int* pre, int nj, int x) {
+  int lo = 0, hi = nj - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// step 1: a cluster of CS CTAs per matrix (CS = 1: one CTA).  Per column k every
+// CTA reads row k and forms the same reflector (the same reductions in the same
+// order); the rows of the trailing block are dealt out warp by warp over the
+// cluster for p = tau A22 v and for the rank-2 update, p is exchanged through
+// global scratch, and two cluster barriers per column order the steps (p complete
+// before it is read; the update complete before row k + 1 is read and before p is
+// overwritten).  The reflector goes to U (row k), so no CTA writes a row another
+// may still be reading.
+__device__ __forceinline__ uint32_t syev_cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void syev_cluster_sync() {
+  __threadfence();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int CS>
+__global__ void __launch_bounds__(SYEV_THREADS) syev_tridiag_kernel(const SyevJob* jobs, const int* sel, int maxn) {
+  const int rank = CS > 1 ? int(syev_cluster_rank()) : 0;
+  const SyevJob jb = jobs[sel[blockIdx.x / CS]];
   const int n = jb.n;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   extern __shared__ double sm[];
   double* vs = sm;             // Householder vector of the current step
   double* ps = vs + maxn;      // p = tau A22 v, then w
-  double* dd = ps + maxn;      // diagonal of T, then eigenvalues
-  double* ee = dd + maxn;      // off-diagonal of T (ee[i] couples i and i + 1)
-  double* tt = ee + maxn;      // tau_k
-  double* rc = tt + maxn;      // rotation cosines of one QL iteration
-  double* rs = rc + maxn;      // rotation sines
-  double* red = rs + maxn;     // 40 doubles: reductions and scalars
-  int* ri = reinterpret_cast<int*>(red + 40);   // rotation column indices
+  double* red = ps + maxn;     // 40 doubles: reductions and scalars
   double* A = jb.A;
-  double* Zc = jb.Z;           // column-major working copy: Zc[c * n + r]
-
-  // ---- 1. tridiagonalisation
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
-    double* x = A + int64_t(k) * n + k + 1;          // row k right of the diagonal (= column k below it)
+    const double* x = A + int64_t(k) * n + k + 1;    // row k right of the diagonal (= column k below it)
     double part = 0.0;
     for (int i = 1 + tid; i < m; i += nt) part += x[i] * x[i];
     const double sigma = block_sum(part, red);
     if (tid == 0) {
       const double alpha = x[0];
-      dd[k] = A[int64_t(k) * n + k];
-      if (sigma == 0.0) {
-        tt[k] = 0.0;
-        ee[k] = alpha;
-        red[34] = 0.0;
-      } else {
+      double beta = alpha, tau = 0.0, scale = 0.0;
+      if (sigma != 0.0) {
         const double mu = sqrt(alpha * alpha + sigma);
-        const double beta = alpha <= 0.0 ? mu : -mu;
-        tt[k] = (beta - alpha) / beta;
-        ee[k] = beta;
-        red[34] = 1.0 / (alpha - beta);
+        beta = alpha <= 0.0 ? mu : -mu;
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      red[34] = scale;
+      red[35] = tau;
+      if (rank == 0) {
+        jb.d[k] = A[int64_t(k) * n + k];
+        jb.e[k] = beta;
+        jb.tau[k] = tau;
       }
     }
     __syncthreads();
-    const double tau = tt[k], scale = red[34];
-    if (tau == 0.0) {
-      if (tid == 0) x[0] = 1.0;
-      __syncthreads();
-      continue;
-    }
+    const double tau = red[35], scale = red[34];
+    if (tau == 0.0) continue;   // H_k = I: A unchanged
+    double* u = jb.U + int64_t(k) * n + k + 1;
     for (int i = tid; i < m; i += nt) {
       const double v = i == 0 ? 1.0 : x[i] * scale;
       vs[i] = v;
-      x[i] = v;   // the reflector is kept in row k for step 2
+      if (rank == 0) u[i] = v;   // the reflector, for step 2
     }
     __syncthreads();
-    // p = tau A22 v: one warp per row, lanes along the row
+    // p = tau A22 v: one warp per row, rows dealt out over the cluster's warps
     double* A22 = A + int64_t(k + 1) * n + k + 1;
-    for (int r = wid; r < m; r += nw) {
+    for (int r = rank * nw + wid; r < m; r += CS * nw) {
       const double* row = A22 + int64_t(r) * n;
       double acc = 0.0;
       for (int j = lane; j < m; j += 32) acc += row[j] * vs[j];
       acc = warp_sum(acc);
-      if (lane == 0) ps[r] = tau * acc;
+      if (lane == 0) {
+        if (CS > 1) jb.pb[r] = tau * acc;
+        else ps[r] = tau * acc;
+      }
+    }
+    if (CS > 1) {
+      syev_cluster_sync();
+      for (int i = tid; i < m; i += nt) ps[i] = jb.pb[i];
     }
     __syncthreads();
     double pv = 0.0;
@@ -497,55 +548,132 @@ __global__ void __launch_bounds__(SYEV_THREADS) syev_kernel(const SyevJob* jobs,
     const double K = 0.5 * tau * block_sum(pv, red);
     for (int i = tid; i < m; i += nt) ps[i] -= K * vs[i];   // w
     __syncthreads();
-    // A22 -= v w^T + w v^T
-    for (int r = wid; r < m; r += nw) {
+    // A22 -= v w^T + w v^T on the same rows
+    for (int r = rank * nw + wid; r < m; r += CS * nw) {
       double* row = A22 + int64_t(r) * n;
       const double vr = vs[r], wr = ps[r];
       for (int j = lane; j < m; j += 32) row[j] -= vr * ps[j] + wr * vs[j];
     }
-    __syncthreads();
+    if (CS > 1) syev_cluster_sync();
+    else __syncthreads();
   }
-  if (tid == 0) {
+  if (tid == 0 && rank == 0) {
     if (n >= 2) {
-      dd[n - 2] = A[int64_t(n - 2) * n + n - 2];
-      ee[n - 2] = A[int64_t(n - 2) * n + n - 1];
+      jb.d[n - 2] = A[int64_t(n - 2) * n + n - 2];
+      jb.e[n - 2] = A[int64_t(n - 2) * n + n - 1];
     }
-    dd[n - 1] = A[int64_t(n - 1) * n + n - 1];
-    ee[n - 1] = 0.0;
+    jb.d[n - 1] = A[int64_t(n - 1) * n + n - 1];
+    jb.e[n - 1] = 0.0;
   }
-  // ---- 2. Q = H_0 ... H_{n-3}, accumulated backwards into Zc
-  for (int64_t e = tid; e < int64_t(n) * n; e += nt) Zc[e] = (e / n == e % n) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int k = n - 3; k >= 0; --k) {
-    const double tau = tt[k];
+}
+
+// step 2: one warp per column of Q (pre: prefix sums of the matrices' n)
+__global__ void __launch_bounds__(256) syev_qform_kernel(const SyevJob* jobs, const int* pre, int nj) {
+  const int gw = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (gw >= pre[nj]) return;
+  const int b = syev_find(pre, nj, gw);
+  const SyevJob jb = jobs[b];
+  const int n = jb.n, j = gw - pre[b];
+  double* z = jb.Zc + int64_t(j) * n;
+  for (int i = lane; i < n; i += 32) z[i] = (i == j) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int k = min(j - 1, n - 3); k >= 0; --k) {
+    const double tau = jb.tau[k];
     if (tau == 0.0) continue;
     const int m = n - k - 1;
-    const double* u = A + int64_t(k) * n + k + 1;
-    for (int i = tid; i < m; i += nt) vs[i] = u[i];
-    __syncthreads();
-    // y_j = sum_i u_i Q22[i, j] (column j of Q22 contiguous), then Q22 -= tau u y^T
-    for (int j = wid; j < m; j += nw) {
-      double* col = Zc + int64_t(k + 1 + j) * n + k + 1;
-      double acc = 0.0;
-      for (int i = lane; i < m; i += 32) acc += vs[i] * col[i];
-      acc = tau * warp_sum(acc);
-      for (int i = lane; i < m; i += 32) col[i] -= acc * vs[i];
-    }
-    __syncthreads();
+    const double* u = jb.U + int64_t(k) * n + k + 1;   // u[0] = 1
+    double* zz = z + k + 1;
+    double acc = 0.0;
+    for (int i = lane; i < m; i += 32) acc += u[i] * zz[i];
+    acc = tau * warp_sum(acc);
+    for (int i = lane; i < m; i += 32) zz[i] -= acc * u[i];
+    __syncwarp();
   }
-  // ---- 3. implicit QL on (dd, ee), rotations applied to the columns of Zc
+}
+
+// The rotations of nh recorded QL iterations applied in order to row r of the
+// column-major Zc.  Iteration h rotates the column pairs (i, i + 1) for
+// i = i0, i0 - 1, ..., i0 - count + 1; row r's entry of column i + 1 is final after
+// rotation i, the new entry of column i is carried to the next rotation.  Entries
+// are loaded eight rotations ahead (a column is read before the chain writes it).
+__device__ void syev_apply_row(const double2* __restrict__ rot, const int4* __restrict__ hdr, int nh,
+                               double* Zc, int n, int r) {
+  for (int h = 0; h < nh; ++h) {
+    const int4 hd = hdr[h];
+    const int i0 = hd.x, cnt = hd.y;
+    const double2* rs = rot + hd.z;
+    double zi1 = Zc[int64_t(i0 + 1) * n + r];
+    int q = 0;
+    if (cnt >= 8) {
+      double zc[8];
+      double2 cc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        zc[u] = Zc[int64_t(i0 - u) * n + r];
+        cc[u] = rs[u];
+      }
+      for (; q + 8 <= cnt; q += 8) {
+        const bool more = q + 16 <= cnt;
+        double zn[8];
+        double2 cn[8];
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            zn[u] = Zc[int64_t(i0 - q - 8 - u) * n + r];
+            cn[u] = rs[q + 8 + u];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const double c = cc[u].x, s = cc[u].y;
+          Zc[int64_t(i0 - q - u + 1) * n + r] = s * zc[u] + c * zi1;
+          zi1 = c * zc[u] - s * zi1;
+        }
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            zc[u] = zn[u];
+            cc[u] = cn[u];
+          }
+        }
+      }
+    }
+    for (; q < cnt; ++q) {
+      const double c = rs[q].x, s = rs[q].y;
+      const double zi = Zc[int64_t(i0 - q) * n + r];
+      Zc[int64_t(i0 - q + 1) * n + r] = s * zi + c * zi1;
+      zi1 = c * zi - s * zi1;
+    }
+    Zc[int64_t(i0 - cnt + 1) * n + r] = zi1;
+  }
+}
+
+// step 3: one warp per matrix; lane 0 runs the recurrences and records the
+// rotations; when the record is full, the warp applies it to Zc and starts over.
+// On non-convergence (more than 60 QL iterations for one eigenvalue) *err
+// receives 9.
+__global__ void __launch_bounds__(32) syev_ql_kernel(const SyevJob* jobs, int maxn, int* err) {
+  const SyevJob jb = jobs[blockIdx.x];
+  const int n = jb.n, lane = threadIdx.x;
+  extern __shared__ double sm[];
+  double* dd = sm;
+  double* ee = dd + maxn;
+  for (int i = lane; i < n; i += 32) {
+    dd[i] = jb.d[i];
+    ee[i] = jb.e[i];
+  }
+  __syncwarp();
   // a coupling is negligible relative to its neighbours or to the norm of T (the
   // second test deflates the rounding-level couplings of a numerically singular
   // block, e.g. the null space of a density matrix; backward stable either way)
   const double eps = 2.220446049250313e-16;
-  int l = 0, iter = 0;   // used by thread 0 only
   double tnorm = 0.0;
-  if (tid == 0)
+  int l = 0, iter = 0, nrot = 0, nhdr = 0;   // lane 0's state
+  if (lane == 0)
     for (int i = 0; i < n; ++i) tnorm = fmax(tnorm, fabs(dd[i]) + fabs(ee[i]) + (i ? fabs(ee[i - 1]) : 0.0));
-  int* ctl = ri + maxn;
   for (;;) {
-    if (tid == 0) {
-      int nrot = -1;
+    int full = 0;
+    if (lane == 0) {
       while (l < n) {
         int mm = l;
         for (; mm < n - 1; ++mm)
@@ -554,6 +682,10 @@ __global__ void __launch_bounds__(SYEV_THREADS) syev_kernel(const SyevJob* jobs,
           ++l;
           iter = 0;
           continue;
+        }
+        if (nrot + (mm - l) > jb.rcap || nhdr >= jb.hcap) {
+          full = 1;
+          break;
         }
         if (++iter > 60) {
           atomicExch(err, 9);
@@ -565,75 +697,102 @@ __global__ void __launch_bounds__(SYEV_THREADS) syev_kernel(const SyevJob* jobs,
         g = dd[mm] - dd[l] + ee[l] / (g + (g >= 0.0 ? r : -r));
         double s = 1.0, c = 1.0, p = 0.0;
         bool split = false;
-        nrot = 0;
+        int cnt = 0;
+        double2* rr = jb.rot + nrot;
+        double e_i = ee[mm - 1], d_i = dd[mm - 1], d_i1 = dd[mm];
         for (int i = mm - 1; i >= l; --i) {
-          const double f = s * ee[i], b = c * ee[i];
-          r = hypot(f, g);
+          const double e_n = i > l ? ee[i - 1] : 0.0, d_n = i > l ? dd[i - 1] : 0.0;
+          const double f = s * e_i, b = c * e_i;
+          const double q = fma(g, g, f * f);
+          double t;
+          if (q > 1e-280 && q < 1e280) {
+            t = rsqrt(q);
+            r = q * t;
+          } else {
+            r = hypot(f, g);
+            t = r != 0.0 ? 1.0 / r : 0.0;
+          }
           ee[i + 1] = r;
           if (r == 0.0) {   // the block splits: restart on the smaller one
-            dd[i + 1] -= p;
+            dd[i + 1] = d_i1 - p;
             ee[mm] = 0.0;
             split = true;
             break;
           }
-          s = f / r;
-          c = g / r;
-          g = dd[i + 1] - p;
-          r = (dd[i] - g) * s + 2.0 * c * b;
+          s = f * t;
+          c = g * t;
+          g = d_i1 - p;
+          r = (d_i - g) * s + 2.0 * c * b;
           p = s * r;
           dd[i + 1] = g + p;
           g = c * r - b;
-          rc[nrot] = c;
-          rs[nrot] = s;
-          ri[nrot] = i;
-          ++nrot;
+          rr[cnt++] = make_double2(c, s);
+          e_i = e_n;
+          d_i1 = d_i;
+          d_i = d_n;
         }
         if (!split) {
           dd[l] -= p;
           ee[l] = g;
           ee[mm] = 0.0;
         }
-        break;
-      }
-      ctl[0] = (l < n) ? nrot : -1;
-    }
-    __syncthreads();
-    const int nrot = ctl[0];
-    if (nrot < 0) break;
-    if (nrot > 0) {
-      // rotation q mixes columns i = ri[q] and i + 1; they come in descending i, so
-      // column i + 1 of rotation q is column i of rotation q - 1
-      for (int r = tid; r < n; r += nt) {
-        int i = ri[0];
-        double zi1 = Zc[int64_t(i + 1) * n + r];
-        for (int q = 0; q < nrot; ++q) {
-          i = ri[q];
-          const double c = rc[q], s = rs[q];
-          const double zi = Zc[int64_t(i) * n + r];
-          Zc[int64_t(i + 1) * n + r] = s * zi + c * zi1;
-          zi1 = c * zi - s * zi1;
+        if (cnt > 0) {
+          jb.hdr[nhdr] = make_int4(mm - 1, cnt, nrot, 0);
+          nrot += cnt;
+          ++nhdr;
         }
-        Zc[int64_t(i) * n + r] = zi1;
       }
     }
-    __syncthreads();
+    full = __shfl_sync(0xffffffffu, full, 0);
+    if (!full) break;
+    const int nh = __shfl_sync(0xffffffffu, nhdr, 0);
+    __syncwarp();
+    for (int r = lane; r < n; r += 32) syev_apply_row(jb.rot, jb.hdr, nh, jb.Zc, n, r);
+    __syncwarp();
+    nrot = 0;
+    nhdr = 0;
   }
-  // ---- 4. sort ascending (rank of each eigenvalue); permuted columns go through A
-  double* dg = work_d + int64_t(blockIdx.x) * maxn;
-  for (int i = tid; i < n; i += nt) dg[i] = dd[i];
-  __syncthreads();
-  for (int i = tid; i < n; i += nt) {
-    int r = 0;
-    const double di = dg[i];
-    for (int j = 0; j < n; ++j) {
-      const double dj = dg[j];
-      r += (dj < di) || (dj == di && j < i);
-    }
-    jb.w[r] = di;
-    for (int row = 0; row < n; ++row) A[int64_t(row) * n + r] = Zc[int64_t(i) * n + row];
+  if (lane == 0) *jb.nh = nhdr;
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) jb.d[i] = dd[i];
+}
+
+// step 4: one warp per 32 rows of one matrix (pre: prefix sums of ceil(n / 32))
+__global__ void __launch_bounds__(256) syev_rot_kernel(const SyevJob* jobs, const int* pre, int nj) {
+  const int gw = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (gw >= pre[nj]) return;
+  const int b = syev_find(pre, nj, gw);
+  const SyevJob jb = jobs[b];
+  const int r = (gw - pre[b]) * 32 + lane;
+  if (r < jb.n) syev_apply_row(jb.rot, jb.hdr, *jb.nh, jb.Zc, jb.n, r);
+}
+
+// step 5a: rank of every eigenvalue (ties by index); w in ascending order
+__global__ void __launch_bounds__(256) syev_sort_kernel(const SyevJob* jobs, const int* pre, int nj) {
+  const int g = int(blockIdx.x * blockDim.x + threadIdx.x);
+  if (g >= pre[nj]) return;
+  const int b = syev_find(pre, nj, g);
+  const SyevJob jb = jobs[b];
+  const int i = g - pre[b];
+  const double di = jb.d[i];
+  int r = 0;
+  for (int j = 0; j < jb.n; ++j) {
+    const double dj = jb.d[j];
+    r += (dj < di) || (dj == di && j < i);
   }
-  __syncthreads();
-  for (int64_t e = tid; e < int64_t(n) * n; e += nt) jb.Z[e] = A[e];
+  jb.w[r] = di;
+  jb.perm[i] = r;
+}
+
+// step 5b: one CTA per eigenvector: column i of Zc to column perm[i] of Z
+__global__ void __launch_bounds__(128) syev_perm_kernel(const SyevJob* jobs, const int* pre, int nj) {
+  const int g = int(blockIdx.x);
+  const int b = syev_find(pre, nj, g);
+  const SyevJob jb = jobs[b];
+  const int n = jb.n, i = g - pre[b];
+  const int to = jb.perm[i];
+  const double* src = jb.Zc + int64_t(i) * n;
+  for (int row = threadIdx.x; row < n; row += blockDim.x) jb.Z[int64_t(row) * n + to] = src[row];
 }
 
 // Rayleigh-Ritz of the Davidson subspace: lowest eigenpair of an m x m matrix (m <= 40)
@@ -1120,22 +1279,116 @@ class CudaExec : public Exec {
     launch(PROF_EIG, [&] { ritz_kernel<<<1, 64, 0, st_>>>(H, ldh, m, theta, y); });
   }
   void syev(const std::vector<double*>& A, const std::vector<double*>& w, const std::vector<double*>& Z,
-            const std::vector<int>& n) override {
+            const std::vector<int>& n, int rot_cap) override {
     if (A.empty()) return;
-    std::vector<SyevJob> jobs;
+    const int nj = int(A.size());
+    // per matrix: d, e, tau, pb (4n), Zc, U (2 n^2), rotation record (2 rcap) doubles;
+    // headers (4 hcap), perm (n), header count (4) ints; every part 16-byte aligned
+    auto up2 = [](int64_t x) { return (x + 1) & ~int64_t(1); };
+    auto up4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
+    std::vector<int64_t> doff(nj), ioff(nj);
+    std::vector<int> rcap(nj), hcap(nj), pre_n(nj + 1, 0), pre_s(nj + 1, 0);
+    int64_t dtot = 0, itot = 0;
     int maxn = 2;
-    for (size_t i = 0; i < A.size(); ++i) {
-      jobs.push_back(SyevJob{A[i], w[i], Z[i], n[i], 0});
-      maxn = std::max(maxn, n[i] + 2);
+    for (int j = 0; j < nj; ++j) {
+      const int64_t m = n[j];
+      if (m <= 0) throw std::runtime_error("syev: empty matrix");
+      // QL takes about n^2 / 2 rotations; a fuller record is applied and restarted
+      rcap[j] = int(std::min<int64_t>(std::max<int64_t>(m * m, 64), int64_t(1) << 26));
+      if (rot_cap > 0) rcap[j] = std::min(rcap[j], std::max(rot_cap, int(m)));
+      hcap[j] = int(4 * m + 64);
+      doff[j] = dtot;
+      dtot += up2(4 * m) + 2 * up2(m * m) + 2 * int64_t(rcap[j]);
+      ioff[j] = itot;
+      itot += 4 * int64_t(hcap[j]) + up4(m) + 4;
+      pre_n[j + 1] = pre_n[j] + int(m);
+      pre_s[j + 1] = pre_s[j] + int((m + 31) / 32);
+      maxn = std::max(maxn, int(m) + 2);
     }
+    const size_t smem1 = sizeof(double) * (2 * size_t(maxn) + 40);
+    const size_t smem3 = sizeof(double) * 2 * size_t(maxn);
+    if (smem1 > 227 * 1024) throw std::runtime_error("syev: matrix too large for the shared-memory workspace");
+    double* dw = static_cast<double*>(alloc(sizeof(double) * size_t(dtot)));
+    int* iw = static_cast<int*>(alloc(sizeof(int) * size_t(itot)));
+    std::vector<SyevJob> jobs(nj);
+    for (int j = 0; j < nj; ++j) {
+      const int64_t m = n[j];
+      SyevJob& jb = jobs[j];
+      double* p = dw + doff[j];
+      jb.A = A[j];
+      jb.w = w[j];
+      jb.Z = Z[j];
+      jb.d = p;
+      jb.e = p + m;
+      jb.tau = p + 2 * m;
+      jb.pb = p + 3 * m;
+      p += up2(4 * m);
+      jb.Zc = p;
+      p += up2(m * m);
+      jb.U = p;
+      p += up2(m * m);
+      jb.rot = reinterpret_cast<double2*>(p);
+      int* q = iw + ioff[j];
+      jb.hdr = reinterpret_cast<int4*>(q);
+      q += 4 * int64_t(hcap[j]);
+      jb.perm = q;
+      q += up4(m);
+      jb.nh = q;
+      jb.n = int(m);
+      jb.rcap = rcap[j];
+      jb.hcap = hcap[j];
+      jb.pad = 0;
+    }
+    // the reduction: a cluster of SYEV_CLUSTER CTAs for each matrix of order >= 256,
+    // one CTA for each smaller one
+    std::vector<int> small, big;
+    for (int j = 0; j < nj; ++j) (n[j] >= 256 ? big : small).push_back(j);
     SyevJob* dj = upload(jobs);
-    double* wd = static_cast<double*>(alloc(sizeof(double) * size_t(maxn) * jobs.size()));
-    size_t smem = sizeof(double) * (7 * size_t(maxn) + 40) + sizeof(int) * (size_t(maxn) + 4);
-    if (smem > 227 * 1024) throw std::runtime_error("syev: matrix too large for the shared-memory workspace");
-    if (smem > 48 * 1024) CK(cudaFuncSetAttribute(syev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    launch(PROF_EIG, [&] { syev_kernel<<<unsigned(jobs.size()), SYEV_THREADS, smem, st_>>>(dj, err_, wd, maxn); });
+    int* dpn = upload(pre_n);
+    int* dps = upload(pre_s);
+    int* dsmall = upload(small);
+    int* dbig = upload(big);
+    if (smem1 > 48 * 1024) {
+      CK(cudaFuncSetAttribute(syev_tridiag_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem1)));
+      CK(cudaFuncSetAttribute(syev_tridiag_kernel<SYEV_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(smem1)));
+    }
+    if (smem3 > 48 * 1024)
+      CK(cudaFuncSetAttribute(syev_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem3)));
+    const int ncol = pre_n[nj], nslab = pre_s[nj];
+    if (!small.empty())
+      launch(PROF_EIG, [&] {
+        syev_tridiag_kernel<1><<<unsigned(small.size()), SYEV_THREADS, smem1, st_>>>(dj, dsmall, maxn);
+      });
+    if (!big.empty())
+      launch(PROF_EIG, [&] {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(big.size() * SYEV_CLUSTER));
+        cfg.blockDim = dim3(SYEV_THREADS);
+        cfg.dynamicSmemBytes = smem1;
+        cfg.stream = st_;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = SYEV_CLUSTER;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, syev_tridiag_kernel<SYEV_CLUSTER>, static_cast<const SyevJob*>(dj),
+                              static_cast<const int*>(dbig), maxn));
+      });
+    launch(PROF_EIG, [&] { syev_qform_kernel<<<unsigned((ncol + 7) / 8), 256, 0, st_>>>(dj, dpn, nj); });
+    launch(PROF_EIG, [&] { syev_ql_kernel<<<unsigned(nj), 32, smem3, st_>>>(dj, maxn, err_); });
+    launch(PROF_EIG, [&] { syev_rot_kernel<<<unsigned((nslab + 7) / 8), 256, 0, st_>>>(dj, dps, nj); });
+    launch(PROF_EIG, [&] { syev_sort_kernel<<<unsigned((ncol + 255) / 256), 256, 0, st_>>>(dj, dpn, nj); });
+    launch(PROF_EIG, [&] { syev_perm_kernel<<<unsigned(ncol), 128, 0, st_>>>(dj, dpn, nj); });
     release(dj);
-    release(wd);
+    release(dpn);
+    release(dps);
+    release(dsmall);
+    release(dbig);
+    release(dw);
+    release(iw);
   }
 
  private:
