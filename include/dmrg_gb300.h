@@ -201,13 +201,17 @@ dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_sch
 dmrg_status dmrg_sweep_log(dmrg_handle* h, int32_t* n_steps, const double** rows, int32_t* n_kept,
                            const int32_t** kept);
 
-/* Wall seconds of the last dmrg_sweep call split by phase, in the categories of
- * the paper's timing breakdown (Sec. 4.1): seconds5[0] Tables (sigma plans and
- * split operands), [1] Diag_H (Davidson), [2] SVD (density matrices, Jacobi
+/* Seconds of the last dmrg_sweep call split by phase, in the categories of the
+ * paper's timing breakdown (Sec. 4.1): seconds5[0] Tables (sigma plans and
+ * split operands), [1] Diag_H (Davidson), [2] SVD (density matrices,
  * eigensolver, selection), [3] Ren_l / Ren_r (renormalisation and enlargement of
- * block operators), [4] StVec (wave function moved to the next bond).  The
- * stream is synchronised at every phase boundary while a sweep runs, so the
- * phases add up to the sweep's wall time.  seconds5 is host memory. */
+ * block operators), [4] StVec (wave function moved to the next bond).  Each
+ * phase boundary records a timestamp on the handle's stream (no
+ * synchronisation, so the host builds the next plans while the device still
+ * works); a phase is the advance of the device timeline between its boundaries:
+ * the device work the phase issued, plus the time the device waited for the host
+ * to issue it.  The phases add up to the sweep's wall time on the device.
+ * seconds5 is host memory. */
 dmrg_status dmrg_sweep_phases(dmrg_handle* h, double* seconds5);
 
 /* Adjoint of the sigma step (the differentiation form; Sec. 2.2 uses the

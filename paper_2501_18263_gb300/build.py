@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs, cmds = [], []
     for src in cpp:
         obj = os.path.join(OUT, os.path.basename(src) + ".o")
-        cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function",
+        cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-function",
                      "-I" + os.path.join(os.path.dirname(os.path.dirname(nvcc)), "include"), "-c", src, "-o", obj])
         objs.append(obj)
     for src in cu:

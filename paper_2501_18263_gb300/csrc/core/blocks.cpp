@@ -500,15 +500,19 @@ std::map<OpKey, EnlOpBuild<N>> collect_blocking(const Problem& P, bool left, con
 
   std::map<OpKey, EnlOpBuild<N>> build;
   std::vector<OpKey> keys = left ? left_keys(site + 1, L) : right_keys(site, L);
-  for (const OpKey& k : keys) {
-    EnlOpBuild<N>& t = build[k];
-    key_qn(k, t.op.delta, t.op.odd);
+  std::vector<EnlOpBuild<N>*> tp(keys.size());
+  for (size_t i = 0; i < keys.size(); ++i) {
+    tp[i] = &build[keys[i]];
+    key_qn(keys[i], tp[i]->op.delta, tp[i]->op.odd);
   }
+  // every operator's contributions are collected on their own (host threads; the
+  // block, the site operators and the integrals are only read)
 
   if (left) {
     const int nB = 2 * site;  // block spin-orbitals [0, nB)
-    for (const OpKey& k : keys) {
-      EnlOpBuild<N>& t = build[k];
+    host_parallel_for(int(keys.size()), [&](int ki) {
+      const OpKey& k = keys[ki];
+      EnlOpBuild<N>& t = *tp[ki];
       switch (k.type) {
         case OP_H: {
           bl.add(t, G(OP_H, 0), 0, lift<N>(I4), one);
@@ -588,11 +592,12 @@ std::map<OpKey, EnlOpBuild<N>> collect_blocking(const Problem& P, bool left, con
         default:
           throw std::runtime_error("left enlargement: unexpected operator");
       }
-    }
+    });
   } else {
     const int c0 = 2 * (site + 1);  // block spin-orbitals [c0, 2L)
-    for (const OpKey& k : keys) {
-      EnlOpBuild<N>& t = build[k];
+    host_parallel_for(int(keys.size()), [&](int ki) {
+      const OpKey& k = keys[ki];
+      EnlOpBuild<N>& t = *tp[ki];
       switch (k.type) {
         case OP_H: {
           bl.add(t, G(OP_H, 0), 0, lift<N>(I4), one);
@@ -676,7 +681,7 @@ std::map<OpKey, EnlOpBuild<N>> collect_blocking(const Problem& P, bool left, con
         default:
           throw std::runtime_error("right enlargement: unexpected operator");
       }
-    }
+    });
   }
 
   return build;

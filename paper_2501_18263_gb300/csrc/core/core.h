@@ -4,15 +4,56 @@
 // sigma / wave-function-transformation plans, and the Davidson and sweep
 // drivers.  Everything numerical is delegated to an Exec (exec.h).
 #pragma once
+#include <algorithm>
+#include <atomic>
 #include <cstdint>
+#include <exception>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../exec.h"
 
 namespace dmrg {
+
+// Runs f(i) for every i in [0, n) on up to 16 host threads, indices handed out
+// one at a time (the calls must be independent: each writes only its own
+// results).  The first exception is rethrown on the calling thread.
+template <class F>
+void host_parallel_for(int n, F&& f) {
+  int nt = int(std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u));
+  nt = std::min(nt, n);
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next{0};
+  std::exception_ptr err;
+  std::mutex mu;
+  auto work = [&]() {
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n) return;
+      try {
+        f(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> g(mu);
+        if (!err) err = std::current_exception();
+        next.store(n);
+        return;
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  th.reserve(size_t(nt - 1));
+  for (int t = 1; t < nt; ++t) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+  if (err) std::rethrow_exception(err);
+}
 
 struct QN {
   int a = 0, b = 0;  // n_alpha, n_beta
@@ -276,8 +317,10 @@ class Engine {
   // eigensolver, selection), 3 Ren (renormalisation and enlargement), 4 StVec
   double phase_s[5] = {0, 0, 0, 0, 0};
   void set_D(int D) { P_.D = D; }
-  // phase clock: while a sweep is timed, tick(k) charges the time since the last
-  // tick to phase k (the stream is synchronised at every tick)
+  // phase clock: while a sweep is timed, tick(k) charges the advance of the
+  // device timeline since the last tick to phase k (a stream timestamp, no
+  // synchronisation: the host may run ahead and build the next plans while the
+  // device works; the phases are summed from the timestamps when the sweep ends)
   void tick(int k);
   void set_precision(int p) { P_.precision = p; }
   int64_t graph_runs() const { return graph_runs_; }
@@ -297,7 +340,7 @@ class Engine {
 
  private:
   bool timing_ = false;
-  double t_last_ = 0.0;
+  std::vector<std::pair<int, int>> phase_marks_;   // (phase, stamp) at every tick of a timed sweep
   uint64_t plan_gen_ = 0;
   Problem P_;
   Exec* ex_;

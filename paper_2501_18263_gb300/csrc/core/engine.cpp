@@ -775,10 +775,7 @@ void Engine::init_sweep_state() {
 
 void Engine::tick(int k) {
   if (!timing_) return;
-  ex_->sync();
-  const double t = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
-  phase_s[k] += t - t_last_;
-  t_last_ = t;
+  phase_marks_.push_back({k, ex_->stamp()});
 }
 
 std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol, int flags, int max_iter) {
@@ -797,9 +794,25 @@ std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol, i
   sweep_log_.clear();
   mode_log_.clear();
   for (double& x : phase_s) x = 0.0;
-  ex_->sync();
-  t_last_ = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  ex_->stamps_clear();
+  phase_marks_.clear();
+  phase_marks_.push_back({-1, ex_->stamp()});
   timing_ = true;
+  // the phase sums are taken when the sweeps end, also when a step throws
+  struct PhaseSum {
+    Engine* e;
+    ~PhaseSum() {
+      e->timing_ = false;
+      try {
+        for (size_t i = 1; i < e->phase_marks_.size(); ++i)
+          e->phase_s[e->phase_marks_[i].first] +=
+              1e-3 * e->ex_->stamp_ms(e->phase_marks_[i - 1].second, e->phase_marks_[i].second);
+        e->ex_->stamps_clear();
+      } catch (...) {
+      }
+      e->phase_marks_.clear();
+    }
+  } phase_sum{this};
   const bool refine_all = (flags & 1) != 0;
   for (int s = 0; s < nsw; ++s) {
     const int D = Dsched ? Dsched[s] : P_.D;
@@ -841,7 +854,6 @@ std::vector<double> Engine::run_sweeps(int nsw, const int* Dsched, double tol, i
     for (int b = L - 2; b >= 1; --b) step(b, 0, (refine_all || b == 1) ? 1 : 0);  // right to left
     E.push_back(e);
   }
-  timing_ = false;
   return E;
 }
 

@@ -129,9 +129,17 @@ class Exec {
   virtual void release(void* p) = 0;
   virtual void zero(void* p, size_t bytes) = 0;
   virtual void h2d(void* d, const void* h, size_t bytes) = 0;
+  // the same copy issued directly from h (no staging; allocates nothing)
+  virtual void h2d_direct(void* d, const void* h, size_t bytes) = 0;
   virtual void d2h(void* h, const void* d, size_t bytes) = 0;
   virtual void d2d(void* d, const void* s, size_t bytes) = 0;
   virtual void sync() = 0;
+  // stream-ordered timestamps: stamp() records an event on the stream and returns
+  // its index; stamp_ms(a, b) = device milliseconds between two stamps (waits for
+  // b); stamps_clear() synchronises the stream and releases them
+  virtual int stamp() = 0;
+  virtual double stamp_ms(int a, int b) = 0;
+  virtual void stamps_clear() = 0;
 
   // grouped element-wise Kronecker accumulation (operator blocking)
   virtual void kron(const std::vector<KronGroup>& g, const std::vector<KronTask>& t) = 0;

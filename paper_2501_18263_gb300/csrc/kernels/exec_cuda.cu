@@ -833,6 +833,7 @@ class CudaExec : public Exec {
   bool prof_ = false;
   std::vector<Mark> marks_;
   std::vector<cudaEvent_t> pool_;
+  std::vector<cudaEvent_t> stamps_;   // phase timestamps (stamp)
   double acc_[2 * PROF_N] = {};
   cudaEvent_t ev() {
     if (pool_.empty()) {
@@ -900,6 +901,7 @@ class CudaExec : public Exec {
       if (g) cudaGraphExecDestroy(g);
     try { drain(); } catch (...) {}
     for (auto& m : marks_) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+    for (auto e : stamps_) cudaEventDestroy(e);
     for (auto e : pool_) cudaEventDestroy(e);
     for (auto& p : plans_) free_plan_mem(p);
     for (size_t i = 0; i < mplans_.size(); ++i) mix_free(int(i));
@@ -908,6 +910,8 @@ class CudaExec : public Exec {
     cudaStreamSynchronize(st_);
     cudaFree(part_);
     cudaFree(err_);
+    if (stage_ev_) cudaEventDestroy(stage_ev_);
+    if (stage_) cudaFreeHost(stage_);
   }
   int64_t alloc_count() const override { return n_alloc_; }
   void* alloc(size_t b) override {
@@ -926,8 +930,46 @@ class CudaExec : public Exec {
   void zero(void* p, size_t b) override {
     if (b) CK(cudaMemsetAsync(p, 0, b, st_));
   }
-  void h2d(void* d, const void* h, size_t b) override {
+  void h2d_direct(void* d, const void* h, size_t b) override {
     if (b) CK(cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, st_));
+  }
+  // Host-to-device copies go through a pinned staging ring: a copy from pageable
+  // memory first waits for all work queued on the stream, so every plan upload
+  // would stall the host until the GPU caught up.  The ring is filled front to
+  // back; an event recorded after each staged copy marks how far the device has
+  // read it, and the host waits on that event only when the ring wraps (the
+  // stream runs in order, so the last copy done means every earlier one is).
+  // Copies during stream capture, or larger than the ring may grow to, go direct.
+  void h2d(void* d, const void* h, size_t b) override {
+    if (!b) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st_, &cs));
+    const size_t need = (b + 255) & ~size_t(255);
+    if (cs != cudaStreamCaptureStatusNone || need > kStageMax / 2) {
+      CK(cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, st_));
+      return;
+    }
+    if (!stage_ev_) CK(cudaEventCreateWithFlags(&stage_ev_, cudaEventDisableTiming));
+    if (2 * need > stage_cap_) {   // grow (after the device has read what is staged)
+      size_t cap = std::max<size_t>(stage_cap_ ? stage_cap_ : (size_t(32) << 20), 2 * need);
+      cap = std::min(cap, kStageMax);
+      if (stage_) {
+        CK(cudaEventSynchronize(stage_ev_));
+        CK(cudaFreeHost(stage_));
+        stage_ = nullptr;
+      }
+      CK(cudaHostAlloc(reinterpret_cast<void**>(&stage_), cap, cudaHostAllocDefault));
+      stage_cap_ = cap;
+      stage_head_ = 0;
+    } else if (stage_head_ + need > stage_cap_) {
+      CK(cudaEventSynchronize(stage_ev_));
+      stage_head_ = 0;
+    }
+    char* src = stage_ + stage_head_;
+    stage_head_ += need;
+    std::memcpy(src, h, b);
+    CK(cudaMemcpyAsync(d, src, b, cudaMemcpyHostToDevice, st_));
+    CK(cudaEventRecord(stage_ev_, st_));
   }
   void d2h(void* h, const void* d, size_t b) override {
     if (b) {
@@ -939,6 +981,23 @@ class CudaExec : public Exec {
     if (b && d != s) CK(cudaMemcpyAsync(d, s, b, cudaMemcpyDeviceToDevice, st_));
   }
   void sync() override { CK(cudaStreamSynchronize(st_)); }
+  int stamp() override {
+    cudaEvent_t e = ev();
+    stamps_.push_back(e);
+    CK(cudaEventRecord(e, st_));
+    return int(stamps_.size() - 1);
+  }
+  double stamp_ms(int a, int b) override {
+    CK(cudaEventSynchronize(stamps_.at(size_t(b))));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, stamps_.at(size_t(a)), stamps_.at(size_t(b))));
+    return double(ms);
+  }
+  void stamps_clear() override {
+    CK(cudaStreamSynchronize(st_));
+    for (cudaEvent_t e : stamps_) pool_.push_back(e);
+    stamps_.clear();
+  }
 
   template <class T>
   T* upload(const std::vector<T>& v) {
@@ -1396,6 +1455,10 @@ class CudaExec : public Exec {
   int prec_;
   int dev_ = 0, nsm_ = 148;
   int64_t n_alloc_ = 0;
+  static constexpr size_t kStageMax = size_t(512) << 20;   // pinned staging ring: at most 512 MiB
+  char* stage_ = nullptr;
+  size_t stage_cap_ = 0, stage_head_ = 0;
+  cudaEvent_t stage_ev_ = nullptr;
   std::vector<cudaGraphExec_t> graphs_;
   double* part_ = nullptr;
   std::vector<Plan> plans_;

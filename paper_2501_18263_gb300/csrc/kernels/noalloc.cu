@@ -56,7 +56,7 @@ extern "C" dmrg_status dmrg_sigma_host_noalloc(dmrg_handle* h, int32_t bond, con
       base = g_addr[cur];
     }
     dmrg::Exec* ex = h->eng->exec();
-    ex->h2d(base, psi_host, size_t(n) * sizeof(double));
+    ex->h2d_direct(base, psi_host, size_t(n) * sizeof(double));
     // replays the bond's CUDA graph if one was captured earlier; never captures one
     // here (instantiating a graph may allocate)
     h->eng->sigma_precision(base, base + kMaxPsi, h->eng->problem().precision, false);
