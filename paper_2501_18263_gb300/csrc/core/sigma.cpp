@@ -247,11 +247,27 @@ void Engine::build_sigma_plan() {
 
   // fine maps of all operators used
   std::vector<FineMap> fmL(T.size()), fmR(T.size());
-  for (size_t n = 0; n < T.size(); ++n) {
+  host_parallel_for(int(T.size()), [&](int n) {
     fmL[n] = fine_map(T[n].L);
     fmR[n] = fine_map(T[n].R);
-  }
+  });
   auto is_ident = [](const OpBlk* b) { return b->ident != 0; };
+  // problems and segments are built per term (stage 1) or per output block (stage 2)
+  // on host threads, then concatenated in the order a serial build gives
+  struct PartPlan {
+    std::vector<GemmProb> P;
+    std::vector<GemmSeg> S;
+    int64_t flops = 0;
+  };
+  auto append = [](std::vector<GemmProb>& P, std::vector<GemmSeg>& S, const PartPlan& pp) {
+    const int off = int(S.size());
+    for (GemmProb q : pp.P) {
+      q.s0 += off;
+      q.s1 += off;
+      P.push_back(q);
+    }
+    S.insert(S.end(), pp.S.begin(), pp.S.end());
+  };
 
   for (size_t ci = 0; ci < ranges.size(); ++ci) {
     const size_t n0 = ranges[ci].first, n1 = ranges[ci].second;
@@ -264,11 +280,12 @@ void Engine::build_sigma_plan() {
       }
     }
     // ---- stage 1
-    std::vector<GemmProb> P1;
-    std::vector<GemmSeg> S1;
-    for (size_t n = n0; n < n1; ++n) {
+    std::vector<PartPlan> pt(n1 - n0);
+    host_parallel_for(int(n1 - n0), [&](int tn) {
+      const size_t n = n0 + size_t(tn);
+      PartPlan& pp = pt[size_t(tn)];
       const Term& t = T[n];
-      if (!t.L) continue;
+      if (!t.L) return;
       for (const XBlk& xb : xl[n]) {
         const int64_t cols = ER.coarse.dim[xb.jR];
         const QN qL = EL.coarse.q[xb.iL];
@@ -283,34 +300,41 @@ void Engine::build_sigma_plan() {
           q.N = int(cols);
           q.alpha = t.c * sg;
           q.accumulate = 0;
-          q.s0 = int(S1.size());
+          q.s0 = int(pp.S.size());
           for (int f : EL.coarse_fines[xb.iL]) {
             const OpBlk* ob;
             if (!t.Lt) {
               auto it = fmL[n].find({ft, f});
               if (it == fmL[n].end()) continue;
               ob = it->second;
-              S1.push_back(GemmSeg{EopsL_.arena + ob->off, psi + int64_t(EL.f_row[f]) * cols, ob->cols,
+              pp.S.push_back(GemmSeg{EopsL_.arena + ob->off, psi + int64_t(EL.f_row[f]) * cols, ob->cols,
                                    int(cols), EL.f_dim[f], 0, 0});
             } else {
               auto it = fmL[n].find({f, ft});
               if (it == fmL[n].end()) continue;
               ob = it->second;
-              S1.push_back(GemmSeg{EopsL_.arena + ob->off, psi + int64_t(EL.f_row[f]) * cols, ob->cols,
+              pp.S.push_back(GemmSeg{EopsL_.arena + ob->off, psi + int64_t(EL.f_row[f]) * cols, ob->cols,
                                    int(cols), EL.f_dim[f], 1, 0});
             }
-            if (!is_ident(ob)) st_.flops_stage1 += 2 * int64_t(q.M) * q.N * EL.f_dim[f];
+            if (!is_ident(ob)) pp.flops += 2 * int64_t(q.M) * q.N * EL.f_dim[f];
           }
-          q.s1 = int(S1.size());
-          P1.push_back(q);
+          q.s1 = int(pp.S.size());
+          pp.P.push_back(q);
         }
       }
+    });
+    std::vector<GemmProb> P1;
+    std::vector<GemmSeg> S1;
+    for (const PartPlan& pp : pt) {
+      append(P1, S1, pp);
+      st_.flops_stage1 += pp.flops;
     }
     // ---- stage 2
-    std::vector<GemmProb> P2;
-    std::vector<GemmSeg> S2;
-    for (size_t iT = 0; iT < EL.coarse.q.size(); ++iT) {
-      if (psi_off_[iT] < 0) continue;
+    std::vector<PartPlan> pb(EL.coarse.q.size());
+    host_parallel_for(int(EL.coarse.q.size()), [&](int iTi) {
+      const size_t iT = size_t(iTi);
+      if (psi_off_[iT] < 0) return;
+      PartPlan& pp = pb[iT];
       const int jT = psi_rcoarse_[iT];
       const int64_t rows = EL.coarse.dim[iT], colsT = ER.coarse.dim[jT];
       for (int gt : ER.coarse_fines[jT]) {
@@ -321,7 +345,7 @@ void Engine::build_sigma_plan() {
         q.N = ER.f_dim[gt];
         q.alpha = 1.0;
         q.accumulate = ci > 0;
-        q.s0 = int(S2.size());
+        q.s0 = int(pp.S.size());
         for (size_t n = n0; n < n1; ++n) {
           const Term& t = T[n];
           QN dR = t.Rt ? QN{0, 0} - t.R->delta : t.R->delta;
@@ -347,19 +371,25 @@ void Engine::build_sigma_plan() {
               auto it = fmR[n].find({gt, g});
               if (it == fmR[n].end()) continue;
               ob = it->second;
-              S2.push_back(GemmSeg{A + ER.f_row[g], EopsR_.arena + ob->off, int(lda), ob->cols, ER.f_dim[g], 0, 1});
+              pp.S.push_back(GemmSeg{A + ER.f_row[g], EopsR_.arena + ob->off, int(lda), ob->cols, ER.f_dim[g], 0, 1});
             } else {
               auto it = fmR[n].find({g, gt});
               if (it == fmR[n].end()) continue;
               ob = it->second;
-              S2.push_back(GemmSeg{A + ER.f_row[g], EopsR_.arena + ob->off, int(lda), ob->cols, ER.f_dim[g], 0, 0});
+              pp.S.push_back(GemmSeg{A + ER.f_row[g], EopsR_.arena + ob->off, int(lda), ob->cols, ER.f_dim[g], 0, 0});
             }
-            if (!is_ident(ob)) st_.flops_stage2 += 2 * int64_t(q.M) * q.N * ER.f_dim[g];
+            if (!is_ident(ob)) pp.flops += 2 * int64_t(q.M) * q.N * ER.f_dim[g];
           }
         }
-        q.s1 = int(S2.size());
-        P2.push_back(q);
+        q.s1 = int(pp.S.size());
+        pp.P.push_back(q);
       }
+    });
+    std::vector<GemmProb> P2;
+    std::vector<GemmSeg> S2;
+    for (const PartPlan& pp : pb) {
+      append(P2, S2, pp);
+      st_.flops_stage2 += pp.flops;
     }
     Chunk ch;
     ch.plan1 = P1.empty() ? -1 : ex_->gemm_plan(P1, S1);
@@ -614,17 +644,22 @@ void Engine::build_sigma_plan() {
       // share the B operand psi^T{jR, f} and become rows of one tall GEMM (A rows
       // and output rows from per-row tables).  Rows with several contributing f
       // (complementary S_q) are separate problems.
-      std::vector<MixProb> P1;
-      std::vector<MixSeg> S1;
-      std::vector<int64_t> bcol, ccol;
-      std::vector<float> acol;
       // rows come in units of 8 (one 8-row group of a fine operator matrix: its
-      // offset and K-slab stride); c < 0 marks a padding row past the last one
+      // offset and K-slab stride); c < 0 marks a padding row past the last one.
+      // Each term's rows are listed on a host thread (gathered row units with their
+      // fine block f, and dense-row problems), then merged in term order.
       struct GUnit { int64_t b, bs; int64_t c[8]; float a; };
-      std::map<std::tuple<int, int, int>, std::vector<GUnit>> groups;   // (iL, jR, f) -> row units
-      for (size_t n = n0; n < n1; ++n) {
+      struct TermRows {
+        std::vector<std::pair<int, GUnit>> units;
+        std::vector<MixProb> P;
+        std::vector<MixSeg> S;
+      };
+      std::vector<TermRows> trows(n1 - n0);
+      host_parallel_for(int(n1 - n0), [&](int tn) {
+        const size_t n = n0 + size_t(tn);
+        TermRows& out = trows[size_t(tn)];
         const Term& t = T[n];
-        if (!t.L) continue;
+        if (!t.L) return;
         for (size_t k = 0; k < xl[n].size(); ++k) {
           const XBlk& xb = xl[n][k];
           const QN qL = EL.coarse.q[xb.iL];
@@ -644,7 +679,6 @@ void Engine::build_sigma_plan() {
               const int64_t b0 = t.Lt ? ob->pt : ob->pn;
               const int64_t kt = pad32(EL.f_dim[f]);
               const int br8 = int(pad8(EL.f_dim[ft]));   // rows of the fine matrix
-              auto& col = groups[std::make_tuple(xb.iL, xb.jR, f)];
               for (int j8 = 0; j8 < EL.f_dim[ft]; j8 += 8) {
                 const int rb = j8 >> 7, hb = std::min(128, br8 - 128 * rb);
                 GUnit u{b0 + int64_t(rb) * 384 * kt + ((j8 & 127) >> 3) * 768, int64_t(96) * hb, {},
@@ -657,7 +691,7 @@ void Engine::build_sigma_plan() {
                                   (int64_t(hx >> 3) << 48))
                                : -1;
                 }
-                col.push_back(u);
+                out.units.push_back({f, u});
               }
               continue;
             }
@@ -674,39 +708,73 @@ void Engine::build_sigma_plan() {
             q.alpha = float(t.c * sg);
             q.mode = 2;
             q.cm0 = -1;
-            q.s0 = int(S1.size());
+            q.s0 = int(out.S.size());
             for (auto& fb : fs) {
               const int f = fb.first;
               const uint16_t* Ap = oplLf_ + (t.Lt ? fb.second->pt : fb.second->pn);
-              S1.push_back(MixSeg{Ap, psiT_ + tOff[f], EL.f_dim[f], 0});
+              out.S.push_back(MixSeg{Ap, psiT_ + tOff[f], EL.f_dim[f], 0});
             }
-            q.s1 = int(S1.size());
-            P1.push_back(q);
+            q.s1 = int(out.S.size());
+            out.P.push_back(q);
           }
         }
+      });
+      std::vector<MixProb> P1;
+      std::vector<MixSeg> S1;
+      for (const TermRows& x : trows) {   // dense-row problems in term order
+        const int off = int(S1.size());
+        for (MixProb q : x.P) {
+          q.s0 += off;
+          q.s1 += off;
+          P1.push_back(q);
+        }
+        S1.insert(S1.end(), x.S.begin(), x.S.end());
       }
-      for (auto& gk : groups) {
-        const int jR = std::get<1>(gk.first), f = std::get<2>(gk.first);
+      // one gathered problem per fine block f of L' (the psi block and its R'
+      // partner follow from f), in (coarse block, f) order, rows in term order
+      std::vector<int64_t> cnt(EL.f_dim.size(), 0);
+      for (const TermRows& x : trows)
+        for (auto& fu : x.units) ++cnt[size_t(fu.first)];
+      std::vector<int> fo;
+      for (size_t f = 0; f < cnt.size(); ++f)
+        if (cnt[f]) fo.push_back(int(f));
+      std::stable_sort(fo.begin(), fo.end(), [&](int x, int y) { return EL.f_coarse[x] < EL.f_coarse[y]; });
+      std::vector<int64_t> upos(EL.f_dim.size(), 0);
+      int64_t nunits = 0;
+      for (int f : fo) {
+        upos[size_t(f)] = nunits;
+        nunits += cnt[size_t(f)];
+      }
+      std::vector<int64_t> bcol(size_t(2 * nunits)), ccol(size_t(8 * nunits));
+      std::vector<float> acol(size_t(8 * nunits));
+      for (const TermRows& x : trows)
+        for (auto& fu : x.units) {
+          const size_t i = size_t(upos[size_t(fu.first)]++);
+          const GUnit& u = fu.second;
+          bcol[2 * i] = u.b;
+          bcol[2 * i + 1] = u.bs;
+          for (int e = 0; e < 8; ++e) {
+            ccol[8 * i + e] = u.c[e];
+            acol[8 * i + e] = u.a;
+          }
+        }
+      trows.clear();
+      int64_t ubase = 0;
+      for (int f : fo) {
+        const int jR = psi_rcoarse_[EL.f_coarse[f]];
         MixProb q{};
         q.Cp = xpl_;
         q.ldc = colpad[jR];
-        q.M = 8 * int(gk.second.size());
+        q.M = 8 * int(cnt[size_t(f)]);
         q.N = colpad[jR];
         q.alpha = 1.0f;
         q.mode = 3;
-        q.cm0 = int64_t(ccol.size());
-        for (const GUnit& u : gk.second) {
-          bcol.push_back(u.b);
-          bcol.push_back(u.bs);
-          for (int e = 0; e < 8; ++e) {
-            ccol.push_back(u.c[e]);
-            acol.push_back(u.a);
-          }
-        }
+        q.cm0 = 8 * ubase;
         q.s0 = int(S1.size());
         S1.push_back(MixSeg{oplLf_, psiT_ + tOff[f], EL.f_dim[f], 0});
         q.s1 = int(S1.size());
         P1.push_back(q);
+        ubase += cnt[size_t(f)];
       }
       // segments of every sigma block, then split each block's K list into parts
       struct Blk2 { int iT, jT; std::vector<MixSeg> segs; int64_t K = 0; int tiles = 0; };
