@@ -735,12 +735,25 @@ void Engine::enlarge(bool left, const Block& blk, int site, Enlarged& E, OpSet& 
     out.ops[kv.first] = o;
   }
   alloc_opset(out);
-  std::vector<KronGroup> groups;
-  std::vector<KronTask> tasks;
+  // one group per fine block, one task per contribution: every operator's first
+  // group and task from prefix sums, then the lists filled on host threads
+  std::vector<std::pair<const EnlOpBuild<double>*, Op*>> opl;
+  std::vector<int64_t> goff(1, 0), toff(1, 0);
   for (auto& kv : build) {
-    Op& o = out.ops[kv.first];
+    opl.push_back({&kv.second, &out.ops[kv.first]});
+    int64_t nt = 0;
+    for (auto& tg : kv.second.tgt) nt += int64_t(tg.second.size());
+    goff.push_back(goff.back() + int64_t(kv.second.tgt.size()));
+    toff.push_back(toff.back() + nt);
+  }
+  if (toff.back() > int64_t(INT32_MAX)) throw std::runtime_error("enlarge: too many blocking contributions");
+  std::vector<KronGroup> groups(size_t(goff.back()));
+  std::vector<KronTask> tasks(size_t(toff.back()));
+  host_parallel_for(int(opl.size()), [&](int i) {
+    Op& o = *opl[size_t(i)].second;
+    size_t gi = size_t(goff[size_t(i)]), ti = size_t(toff[size_t(i)]);
     size_t bi = 0;
-    for (auto& tg : kv.second.tgt) {
+    for (auto& tg : opl[size_t(i)].first->tgt) {
       OpBlk& b = o.blk[bi++];
       o.by_col[b.c] = int(bi - 1);
       KronGroup g;
@@ -748,7 +761,7 @@ void Engine::enlarge(bool left, const Block& blk, int site, Enlarged& E, OpSet& 
       g.ld = b.cols;
       g.rows = b.rows;
       g.cols = b.cols;
-      g.t0 = int(tasks.size());
+      g.t0 = int(ti);
       g.accumulate = 0;
       for (auto& pd : tg.second) {
         KronTask tk;
@@ -763,12 +776,12 @@ void Engine::enlarge(bool left, const Block& blk, int site, Enlarged& E, OpSet& 
           tk.mode = pd.trans ? 1 : 0;
         }
         tk.coef = pd.coef;
-        tasks.push_back(tk);
+        tasks[ti++] = tk;
       }
-      g.t1 = int(tasks.size());
-      groups.push_back(g);
+      g.t1 = int(ti);
+      groups[gi++] = g;
     }
-  }
+  });
   if (!groups.empty()) ex_->kron(groups, tasks);
 }
 

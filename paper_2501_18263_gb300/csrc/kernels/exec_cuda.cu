@@ -121,19 +121,26 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmTile* __restric
 // ---------------------------------------------------------------------------
 // grouped Kronecker accumulation
 
-struct KronCta {
-  int group, e0;
-};
-constexpr int KRON_CHUNK = 1024;
+constexpr int KRON_CHUNK = 1024;   // elements of one group per CTA
 
-__global__ void __launch_bounds__(256) kron_kernel(const KronCta* __restrict__ ctas,
+// CTA base + b works on chunk base + b - cpre[k] of the group k with
+// cpre[k] <= base + b < cpre[k + 1] (prefix sums of the groups' chunk counts), so
+// the host lists groups only, not CTAs
+__global__ void __launch_bounds__(256) kron_kernel(const int64_t* __restrict__ cpre, int ngroups, int64_t base,
                                                    const KronGroup* __restrict__ groups,
                                                    const KronTask* __restrict__ tasks) {
-  const KronCta c = ctas[blockIdx.x];
-  const KronGroup g = groups[c.group];
+  const int64_t cb = base + blockIdx.x;
+  int lo = 0, hi = ngroups - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cpre[mid] <= cb) lo = mid;
+    else hi = mid - 1;
+  }
+  const KronGroup g = groups[lo];
   const int n = g.rows * g.cols;
-  const int e1 = min(n, c.e0 + KRON_CHUNK);
-  for (int e = c.e0 + threadIdx.x; e < e1; e += blockDim.x) {
+  const int e0 = int((cb - cpre[lo]) * KRON_CHUNK);
+  const int e1 = min(n, e0 + KRON_CHUNK);
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int r = e / g.cols, col = e - r * g.cols;
     double acc = 0.0;
     for (int t = g.t0; t < g.t1; ++t) {
@@ -895,6 +902,20 @@ class CudaExec : public Exec {
     CK(cudaMalloc(&part_, sizeof(double) * 1024 * MDOT_MAX * 4));
     CK(cudaMalloc(&err_, sizeof(int)));
     CK(cudaMemsetAsync(err_, 0, sizeof(int), st_));
+    // stream-ordered allocations come from the device's default pool, which by
+    // default returns freed memory to the system at every synchronisation, so that
+    // each sweep step would map its multi-gigabyte arenas afresh: keep up to a
+    // quarter of the device memory cached while a handle lives (trimmed when it
+    // goes away; a process-local pool attribute)
+    CK(cudaDeviceGetDefaultMemPool(&mpool_, dev_));
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    uint64_t thr = 0;
+    CK(cudaMemPoolGetAttribute(mpool_, cudaMemPoolAttrReleaseThreshold, &thr));
+    if (thr < tot / 4) {
+      thr = tot / 4;
+      CK(cudaMemPoolSetAttribute(mpool_, cudaMemPoolAttrReleaseThreshold, &thr));
+    }
   }
   ~CudaExec() override {
     for (auto& g : graphs_)
@@ -912,6 +933,7 @@ class CudaExec : public Exec {
     cudaFree(err_);
     if (stage_ev_) cudaEventDestroy(stage_ev_);
     if (stage_) cudaFreeHost(stage_);
+    if (mpool_) cudaMemPoolTrimTo(mpool_, 0);
   }
   int64_t alloc_count() const override { return n_alloc_; }
   void* alloc(size_t b) override {
@@ -1008,15 +1030,17 @@ class CudaExec : public Exec {
 
   void kron(const std::vector<KronGroup>& g, const std::vector<KronTask>& t) override {
     if (g.empty()) return;
-    std::vector<KronCta> ctas;
+    if (g.size() > size_t(INT32_MAX)) throw std::runtime_error("kron: too many groups");
+    std::vector<int64_t> cpre(g.size() + 1, 0);
     for (size_t i = 0; i < g.size(); ++i)
-      for (int e = 0; e < g[i].rows * g[i].cols; e += KRON_CHUNK) ctas.push_back(KronCta{int(i), e});
+      cpre[i + 1] = cpre[i] + (int64_t(g[i].rows) * g[i].cols + KRON_CHUNK - 1) / KRON_CHUNK;
+    const int64_t nct = cpre.back();
     KronGroup* dg = upload(g);
     KronTask* dt = upload(t);
-    KronCta* dc = upload(ctas);
-    for (size_t c0 = 0; c0 < ctas.size(); c0 += (1u << 30)) {
-      unsigned nb = unsigned(std::min<size_t>(ctas.size() - c0, 1u << 30));
-      launch(PROF_KRON, [&] { kron_kernel<<<nb, 256, 0, st_>>>(dc + c0, dg, dt); });
+    int64_t* dc = upload(cpre);
+    for (int64_t c0 = 0; c0 < nct; c0 += (int64_t(1) << 30)) {
+      const unsigned nb = unsigned(std::min<int64_t>(nct - c0, int64_t(1) << 30));
+      launch(PROF_KRON, [&] { kron_kernel<<<nb, 256, 0, st_>>>(dc, int(g.size()), c0, dg, dt); });
     }
     release(dg);
     release(dt);
@@ -1455,6 +1479,7 @@ class CudaExec : public Exec {
   int prec_;
   int dev_ = 0, nsm_ = 148;
   int64_t n_alloc_ = 0;
+  cudaMemPool_t mpool_ = nullptr;
   static constexpr size_t kStageMax = size_t(512) << 20;   // pinned staging ring: at most 512 MiB
   char* stage_ = nullptr;
   size_t stage_cap_ = 0, stage_head_ = 0;
