@@ -309,15 +309,14 @@ dmrg_status dmrg_stats(dmrg_handle* h, int64_t* out16);
  * array, every n[b] >= 1), packed one after the other in device memory, row-major:
  * A holds sum_b n[b]^2 doubles (destroyed), Z receives the eigenvectors as columns
  * (same layout, a separate buffer), w receives the eigenvalues of each matrix in
- * ascending order (sum_b n[b] doubles).  Householder tridiagonalisation and
- * implicit QL in FP64, the kernels the truncation step runs.  rot_cap bounds the
- * rotations recorded per matrix before they are applied (0: n[b]^2; smaller values
- * use less scratch memory and more passes).  Returns DMRG_ERR_NOCONV when a QL
- * iteration does not converge (results undefined), DMRG_ERR_ARG on bad arguments.
- * Runs on the handle's stream and device; synchronous.
+ * ascending order (sum_b n[b] doubles, every n[b] <= 6000).  Householder
+ * tridiagonalisation and divide and conquer in FP64 (leaves of at most 32 rows by
+ * implicit QL), the kernels the truncation step runs.  Returns DMRG_ERR_NOCONV
+ * when a leaf's QL iteration does not converge (results undefined), DMRG_ERR_ARG
+ * on bad arguments.  Runs on the handle's stream and device; synchronous.
  */
 dmrg_status dmrg_eigh_batch(dmrg_handle* h, int32_t nmat, const int32_t* n, double* A_dev, double* w_dev,
-                            double* Z_dev, int32_t rot_cap);
+                            double* Z_dev);
 
 /*
  * Mode optimisation (Sec. 2.2, Fig. 1).  A spin-independent rotation of the two

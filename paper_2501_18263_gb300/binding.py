@@ -79,7 +79,7 @@ def load_library(path: str | None = None):
         "dmrg_graph_replays": ([vp, i64p], ctypes.c_int),
         "dmrg_two_site_rotate": ([vp, i32, f64, vp, vp], ctypes.c_int),
         "dmrg_half_renyi": ([vp, i32, vp, dp], ctypes.c_int),
-        "dmrg_eigh_batch": ([vp, i32, ip, vp, vp, vp, i32], ctypes.c_int),
+        "dmrg_eigh_batch": ([vp, i32, ip, vp, vp, vp], ctypes.c_int),
         "dmrg_mode_step": ([vp, dp, dp, dp], ctypes.c_int),
         "dmrg_get_integrals": ([vp, dp, dp], ctypes.c_int),
         "dmrg_mode_log": ([vp, ip, ctypes.POINTER(dp)], ctypes.c_int),
@@ -287,11 +287,11 @@ class Dmrg:
         self._check(self.lib.dmrg_half_renyi(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.byref(x)))
         return x.value
 
-    def eigh_batch(self, n, A_ptr, w_ptr, Z_ptr, rot_cap=0):
+    def eigh_batch(self, n, A_ptr, w_ptr, Z_ptr):
         """eigen-decomposition of packed symmetric matrices (device pointers; A destroyed)"""
         nn = np.ascontiguousarray(n, dtype=np.int32)
         self._check(self.lib.dmrg_eigh_batch(self.h, len(nn), nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.c_void_p(int(A_ptr)),
-                                             ctypes.c_void_p(int(w_ptr)), ctypes.c_void_p(int(Z_ptr)), int(rot_cap)))
+                                             ctypes.c_void_p(int(w_ptr)), ctypes.c_void_p(int(Z_ptr))))
 
     def mode_step(self):
         th, s0, s1 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -435,13 +435,11 @@ dmrg_status dmrg_orbital_gradient(dmrg_handle* h, const double* g1, const double
   });
 }
 
-dmrg_status dmrg_eigh_batch(dmrg_handle* h, int32_t nmat, const int32_t* n, double* A, double* w, double* Z,
-                            int32_t rot_cap) {
+dmrg_status dmrg_eigh_batch(dmrg_handle* h, int32_t nmat, const int32_t* n, double* A, double* w, double* Z) {
   return guard([&]() -> dmrg_status {
     if (!h || !n || !A || !w || !Z) return fail(DMRG_ERR_ARG, "null argument");
     if (nmat <= 0) return fail(DMRG_ERR_ARG, "nmat must be positive");
     if (A == Z) return fail(DMRG_ERR_ARG, "A and Z must be different buffers");
-    if (rot_cap < 0) return fail(DMRG_ERR_ARG, "rot_cap must be >= 0");
     std::vector<double*> Av, wv, Zv;
     std::vector<int> nv;
     int64_t ao = 0, wo = 0;
@@ -454,7 +452,7 @@ dmrg_status dmrg_eigh_batch(dmrg_handle* h, int32_t nmat, const int32_t* n, doub
       ao += int64_t(n[b]) * n[b];
       wo += n[b];
     }
-    h->eng->exec()->syev(Av, wv, Zv, nv, rot_cap);
+    h->eng->exec()->syev(Av, wv, Zv, nv);
     h->eng->exec()->sync();
     return check_device(h);
   });

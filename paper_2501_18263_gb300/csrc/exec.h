@@ -174,12 +174,11 @@ class Exec {
   // lowest eigenpair of the symmetric m x m matrix whose upper triangle is in H (ld ldh):
   // theta[0] = eigenvalue, y[0..m) = eigenvector
   virtual void ritz(const double* H, int ldh, int m, double* theta, double* y) = 0;
-  // batched symmetric eigen-decomposition (Householder tridiagonalisation and
-  // implicit QL, FP64): A_b is n_b x n_b (ld = n_b, destroyed), w_b ascending
-  // eigenvalues, Z_b eigenvectors as columns (ld n_b); rot_cap = QL rotations
-  // recorded per matrix before they are applied (0: n_b^2)
+  // batched symmetric eigen-decomposition (Householder tridiagonalisation, divide
+  // and conquer, FP64): A_b is n_b x n_b (ld = n_b, destroyed), w_b ascending
+  // eigenvalues, Z_b eigenvectors as columns (ld n_b)
   virtual void syev(const std::vector<double*>& A, const std::vector<double*>& w,
-                    const std::vector<double*>& Z, const std::vector<int>& n, int rot_cap = 0) = 0;
+                    const std::vector<double*>& Z, const std::vector<int>& n) = 0;
 
   // split-BF16 tensor-core GEMM plans (tcgen05 / TMEM)
   virtual int mix_plan(const std::vector<MixProb>& p, const std::vector<MixSeg>& s) = 0;

@@ -3,14 +3,14 @@
 //   kron          grouped Kronecker accumulation (operator blocking)
 //   mdot/lincomb  Davidson Gram-Schmidt and Ritz vectors (deterministic reductions)
 //   ritz          cyclic Jacobi eigensolver of the small Rayleigh-Ritz matrix
-//   syev          Householder tridiagonalisation + implicit QL eigensolver of the
-//                 density matrices of the truncation (reduction one CTA per sector
-//                 block; QL recurrence one thread per block, its rotations applied
-//                 by a warp per 32 rows)
+//   syev          density-matrix eigensolver of the truncation: Householder
+//                 tridiagonalisation (a CTA cluster per large sector block), divide
+//                 and conquer on the tridiagonal matrices (tridiag_dc.cu), W = Q V
 // All work is ordered on one stream; allocations are stream-ordered.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -19,6 +19,7 @@
 #include "../exec.h"
 #include "../exec_errors.h"
 #include "mixed.h"
+#include "tridiag_dc.h"
 
 namespace dmrg {
 
@@ -399,45 +400,33 @@ __device__ void jacobi_core(double* A, double* Z, int n, int ld, double* cs, int
   }
 }
 
-// Batched symmetric eigen-decomposition A = Z diag(w) Z^T (FP64), the classical
-// route split into phases, so that only the inherently sequential recurrence runs
-// on one thread and the O(n^3) phases other than the reduction spread over the GPU:
+// Batched symmetric eigen-decomposition A = Z diag(w) Z^T (FP64) in phases that
+// each spread over the GPU (FP64 on this GPU issues one instruction per warp every
+// few tens of cycles, so a sequential recurrence on one thread, such as the QL
+// iteration's chain of plane rotations, would dominate):
 //  1. Householder reduction to tridiagonal form, A = Q T Q^T with
 //     Q = H_0 ... H_{n-3}, H_k = I - tau_k u_k u_k^T (u_k supported on k+1..n-1),
 //     one CTA per small matrix, a cluster of eight per large one (syev_tridiag_kernel);
 //  2. Q formed explicitly, one warp per column: column j of Q is e_j with the
 //     reflectors k < j applied in the order k = j-1, ..., 0 (the reflectors k >= j
 //     leave e_j alone) (syev_qform_kernel);
-//  3. implicit QL iterations with shifts on T (Bowdler, Martin, Reinsch and
-//     Wilkinson, "The QR and QL algorithms for symmetric matrices", Numer. Math.
-//     11 (1968), the tql2 procedure): the scalar recurrences of one matrix on one
-//     thread, which records each iteration's plane rotations instead of applying
-//     them (syev_ql_kernel);
-//  4. the recorded rotations applied to Z = Q: a column rotation acts on every row
-//     alone, so each thread takes one row through all rotations in order, one warp
-//     per 32 rows (syev_rot_kernel);
+//  3. T = V diag(w) V^T by divide and conquer (tridiag_dc.cu: leaves of at most 32
+//     rows by implicit QL on one warp, merges level by level over all matrices);
+//  4. W = Q V, a grouped FP64 GEMM;
 //  5. eigenvalues sorted ascending, eigenvectors permuted with them
 //     (syev_sort_kernel, syev_perm_kernel).
-// A dependent FP64 operation takes tens of cycles on this GPU (a square root or a
-// division hundreds), so the recurrence of step 3 takes one reciprocal square root
-// per rotation: with q = f^2 + g^2 and t = rsqrt(q), r = q t, c = g t, s = f t
-// (hypot and a division where q would under- or overflow), and it keeps the
-// diagonal and off-diagonal entries it walks over in registers.
 struct SyevJob {
-  double* A;      // n x n input, destroyed
+  double* A;      // n x n input, destroyed; then V, the eigenvectors of T (column-major)
   double* w;      // out: n eigenvalues, ascending
   double* Z;      // out: n x n eigenvectors as columns (row-major, ld n)
   double* d;      // n: diagonal of T, then the (unsorted) eigenvalues
   double* e;      // n: off-diagonal of T (e[i] couples i and i + 1)
   double* tau;    // n: reflector scalars
-  double* Zc;     // n x n working copy of Z, column-major: Zc[c * n + r]
-  double* U;      // n x n: reflector k in row k (u_k[k + 1] = 1)
+  double* Zc;     // n x n, column-major (Zc[c * n + r]): Q
+  double* U;      // n x n: reflector k in row k (u_k[k + 1] = 1), then W = Q V (column-major)
   double* pb;     // n: p = tau A22 v exchanged between the CTAs of a cluster
-  double2* rot;   // recorded rotations (c, s), capacity rcap
-  int4* hdr;      // per QL iteration: (first column i0, count, offset in rot, 0), capacity hcap
   int* perm;      // n: sorted position of eigenvalue i
-  int* nh;        // headers left for syev_rot_kernel
-  int n, rcap, hcap, pad;
+  int n, pad;
 };
 
 constexpr int SYEV_THREADS = 1024;
@@ -598,182 +587,6 @@ __global__ void __launch_bounds__(256) syev_qform_kernel(const SyevJob* jobs, co
   }
 }
 
-// The rotations of nh recorded QL iterations applied in order to row r of the
-// column-major Zc.  Iteration h rotates the column pairs (i, i + 1) for
-// i = i0, i0 - 1, ..., i0 - count + 1; row r's entry of column i + 1 is final after
-// rotation i, the new entry of column i is carried to the next rotation.  Entries
-// are loaded eight rotations ahead (a column is read before the chain writes it).
-__device__ void syev_apply_row(const double2* __restrict__ rot, const int4* __restrict__ hdr, int nh,
-                               double* Zc, int n, int r) {
-  for (int h = 0; h < nh; ++h) {
-    const int4 hd = hdr[h];
-    const int i0 = hd.x, cnt = hd.y;
-    const double2* rs = rot + hd.z;
-    double zi1 = Zc[int64_t(i0 + 1) * n + r];
-    int q = 0;
-    if (cnt >= 8) {
-      double zc[8];
-      double2 cc[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        zc[u] = Zc[int64_t(i0 - u) * n + r];
-        cc[u] = rs[u];
-      }
-      for (; q + 8 <= cnt; q += 8) {
-        const bool more = q + 16 <= cnt;
-        double zn[8];
-        double2 cn[8];
-        if (more) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            zn[u] = Zc[int64_t(i0 - q - 8 - u) * n + r];
-            cn[u] = rs[q + 8 + u];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const double c = cc[u].x, s = cc[u].y;
-          Zc[int64_t(i0 - q - u + 1) * n + r] = s * zc[u] + c * zi1;
-          zi1 = c * zc[u] - s * zi1;
-        }
-        if (more) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            zc[u] = zn[u];
-            cc[u] = cn[u];
-          }
-        }
-      }
-    }
-    for (; q < cnt; ++q) {
-      const double c = rs[q].x, s = rs[q].y;
-      const double zi = Zc[int64_t(i0 - q) * n + r];
-      Zc[int64_t(i0 - q + 1) * n + r] = s * zi + c * zi1;
-      zi1 = c * zi - s * zi1;
-    }
-    Zc[int64_t(i0 - cnt + 1) * n + r] = zi1;
-  }
-}
-
-// step 3: one warp per matrix; lane 0 runs the recurrences and records the
-// rotations; when the record is full, the warp applies it to Zc and starts over.
-// On non-convergence (more than 60 QL iterations for one eigenvalue) *err
-// receives 9.
-__global__ void __launch_bounds__(32) syev_ql_kernel(const SyevJob* jobs, int maxn, int* err) {
-  const SyevJob jb = jobs[blockIdx.x];
-  const int n = jb.n, lane = threadIdx.x;
-  extern __shared__ double sm[];
-  double* dd = sm;
-  double* ee = dd + maxn;
-  for (int i = lane; i < n; i += 32) {
-    dd[i] = jb.d[i];
-    ee[i] = jb.e[i];
-  }
-  __syncwarp();
-  // a coupling is negligible relative to its neighbours or to the norm of T (the
-  // second test deflates the rounding-level couplings of a numerically singular
-  // block, e.g. the null space of a density matrix; backward stable either way)
-  const double eps = 2.220446049250313e-16;
-  double tnorm = 0.0;
-  int l = 0, iter = 0, nrot = 0, nhdr = 0;   // lane 0's state
-  if (lane == 0)
-    for (int i = 0; i < n; ++i) tnorm = fmax(tnorm, fabs(dd[i]) + fabs(ee[i]) + (i ? fabs(ee[i - 1]) : 0.0));
-  for (;;) {
-    int full = 0;
-    if (lane == 0) {
-      while (l < n) {
-        int mm = l;
-        for (; mm < n - 1; ++mm)
-          if (fabs(ee[mm]) <= eps * (fabs(dd[mm]) + fabs(dd[mm + 1])) || fabs(ee[mm]) <= eps * tnorm) break;
-        if (mm == l) {
-          ++l;
-          iter = 0;
-          continue;
-        }
-        if (nrot + (mm - l) > jb.rcap || nhdr >= jb.hcap) {
-          full = 1;
-          break;
-        }
-        if (++iter > 60) {
-          atomicExch(err, 9);
-          l = n;
-          break;
-        }
-        double g = (dd[l + 1] - dd[l]) / (2.0 * ee[l]);
-        double r = hypot(g, 1.0);
-        g = dd[mm] - dd[l] + ee[l] / (g + (g >= 0.0 ? r : -r));
-        double s = 1.0, c = 1.0, p = 0.0;
-        bool split = false;
-        int cnt = 0;
-        double2* rr = jb.rot + nrot;
-        double e_i = ee[mm - 1], d_i = dd[mm - 1], d_i1 = dd[mm];
-        for (int i = mm - 1; i >= l; --i) {
-          const double e_n = i > l ? ee[i - 1] : 0.0, d_n = i > l ? dd[i - 1] : 0.0;
-          const double f = s * e_i, b = c * e_i;
-          const double q = fma(g, g, f * f);
-          double t;
-          if (q > 1e-280 && q < 1e280) {
-            t = rsqrt(q);
-            r = q * t;
-          } else {
-            r = hypot(f, g);
-            t = r != 0.0 ? 1.0 / r : 0.0;
-          }
-          ee[i + 1] = r;
-          if (r == 0.0) {   // the block splits: restart on the smaller one
-            dd[i + 1] = d_i1 - p;
-            ee[mm] = 0.0;
-            split = true;
-            break;
-          }
-          s = f * t;
-          c = g * t;
-          g = d_i1 - p;
-          r = (d_i - g) * s + 2.0 * c * b;
-          p = s * r;
-          dd[i + 1] = g + p;
-          g = c * r - b;
-          rr[cnt++] = make_double2(c, s);
-          e_i = e_n;
-          d_i1 = d_i;
-          d_i = d_n;
-        }
-        if (!split) {
-          dd[l] -= p;
-          ee[l] = g;
-          ee[mm] = 0.0;
-        }
-        if (cnt > 0) {
-          jb.hdr[nhdr] = make_int4(mm - 1, cnt, nrot, 0);
-          nrot += cnt;
-          ++nhdr;
-        }
-      }
-    }
-    full = __shfl_sync(0xffffffffu, full, 0);
-    if (!full) break;
-    const int nh = __shfl_sync(0xffffffffu, nhdr, 0);
-    __syncwarp();
-    for (int r = lane; r < n; r += 32) syev_apply_row(jb.rot, jb.hdr, nh, jb.Zc, n, r);
-    __syncwarp();
-    nrot = 0;
-    nhdr = 0;
-  }
-  if (lane == 0) *jb.nh = nhdr;
-  __syncwarp();
-  for (int i = lane; i < n; i += 32) jb.d[i] = dd[i];
-}
-
-// step 4: one warp per 32 rows of one matrix (pre: prefix sums of ceil(n / 32))
-__global__ void __launch_bounds__(256) syev_rot_kernel(const SyevJob* jobs, const int* pre, int nj) {
-  const int gw = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (gw >= pre[nj]) return;
-  const int b = syev_find(pre, nj, gw);
-  const SyevJob jb = jobs[b];
-  const int r = (gw - pre[b]) * 32 + lane;
-  if (r < jb.n) syev_apply_row(jb.rot, jb.hdr, *jb.nh, jb.Zc, jb.n, r);
-}
-
 // step 5a: rank of every eigenvalue (ties by index); w in ascending order
 __global__ void __launch_bounds__(256) syev_sort_kernel(const SyevJob* jobs, const int* pre, int nj) {
   const int g = int(blockIdx.x * blockDim.x + threadIdx.x);
@@ -798,7 +611,7 @@ __global__ void __launch_bounds__(128) syev_perm_kernel(const SyevJob* jobs, con
   const SyevJob jb = jobs[b];
   const int n = jb.n, i = g - pre[b];
   const int to = jb.perm[i];
-  const double* src = jb.Zc + int64_t(i) * n;
+  const double* src = jb.U + int64_t(i) * n;   // W = Q V
   for (int row = threadIdx.x; row < n; row += blockDim.x) jb.Z[int64_t(row) * n + to] = src[row];
 }
 
@@ -1362,34 +1175,29 @@ class CudaExec : public Exec {
     launch(PROF_EIG, [&] { ritz_kernel<<<1, 64, 0, st_>>>(H, ldh, m, theta, y); });
   }
   void syev(const std::vector<double*>& A, const std::vector<double*>& w, const std::vector<double*>& Z,
-            const std::vector<int>& n, int rot_cap) override {
+            const std::vector<int>& n) override {
     if (A.empty()) return;
     const int nj = int(A.size());
-    // per matrix: d, e, tau, pb (4n), Zc, U (2 n^2), rotation record (2 rcap) doubles;
-    // headers (4 hcap), perm (n), header count (4) ints; every part 16-byte aligned
+    // per matrix: d, e, tau, pb (4n), Zc, U (2 n^2) doubles; perm (n) ints; every
+    // part 16-byte aligned
     auto up2 = [](int64_t x) { return (x + 1) & ~int64_t(1); };
     auto up4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
     std::vector<int64_t> doff(nj), ioff(nj);
-    std::vector<int> rcap(nj), hcap(nj), pre_n(nj + 1, 0), pre_s(nj + 1, 0);
+    std::vector<int> pre_n(nj + 1, 0);
     int64_t dtot = 0, itot = 0;
     int maxn = 2;
     for (int j = 0; j < nj; ++j) {
       const int64_t m = n[j];
       if (m <= 0) throw std::runtime_error("syev: empty matrix");
-      // QL takes about n^2 / 2 rotations; a fuller record is applied and restarted
-      rcap[j] = int(std::min<int64_t>(std::max<int64_t>(m * m, 64), int64_t(1) << 26));
-      if (rot_cap > 0) rcap[j] = std::min(rcap[j], std::max(rot_cap, int(m)));
-      hcap[j] = int(4 * m + 64);
+      if (m > 32767) throw std::runtime_error("syev: matrix order above 32767");
       doff[j] = dtot;
-      dtot += up2(4 * m) + 2 * up2(m * m) + 2 * int64_t(rcap[j]);
+      dtot += up2(4 * m) + 2 * up2(m * m);
       ioff[j] = itot;
-      itot += 4 * int64_t(hcap[j]) + up4(m) + 4;
+      itot += up4(m);
       pre_n[j + 1] = pre_n[j] + int(m);
-      pre_s[j + 1] = pre_s[j] + int((m + 31) / 32);
       maxn = std::max(maxn, int(m) + 2);
     }
     const size_t smem1 = sizeof(double) * (2 * size_t(maxn) + 40);
-    const size_t smem3 = sizeof(double) * 2 * size_t(maxn);
     if (smem1 > 227 * 1024) throw std::runtime_error("syev: matrix too large for the shared-memory workspace");
     double* dw = static_cast<double*>(alloc(sizeof(double) * size_t(dtot)));
     int* iw = static_cast<int*>(alloc(sizeof(int) * size_t(itot)));
@@ -1409,26 +1217,16 @@ class CudaExec : public Exec {
       jb.Zc = p;
       p += up2(m * m);
       jb.U = p;
-      p += up2(m * m);
-      jb.rot = reinterpret_cast<double2*>(p);
-      int* q = iw + ioff[j];
-      jb.hdr = reinterpret_cast<int4*>(q);
-      q += 4 * int64_t(hcap[j]);
-      jb.perm = q;
-      q += up4(m);
-      jb.nh = q;
+      jb.perm = iw + ioff[j];
       jb.n = int(m);
-      jb.rcap = rcap[j];
-      jb.hcap = hcap[j];
       jb.pad = 0;
     }
-    // the reduction: a cluster of SYEV_CLUSTER CTAs for each matrix of order >= 256,
-    // one CTA for each smaller one
+    // 1. the reduction: a cluster of SYEV_CLUSTER CTAs for each matrix of order >= 256,
+    // one CTA for each smaller one; 2. Q
     std::vector<int> small, big;
     for (int j = 0; j < nj; ++j) (n[j] >= 256 ? big : small).push_back(j);
     SyevJob* dj = upload(jobs);
     int* dpn = upload(pre_n);
-    int* dps = upload(pre_s);
     int* dsmall = upload(small);
     int* dbig = upload(big);
     if (smem1 > 48 * 1024) {
@@ -1436,9 +1234,7 @@ class CudaExec : public Exec {
       CK(cudaFuncSetAttribute(syev_tridiag_kernel<SYEV_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(smem1)));
     }
-    if (smem3 > 48 * 1024)
-      CK(cudaFuncSetAttribute(syev_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem3)));
-    const int ncol = pre_n[nj], nslab = pre_s[nj];
+    const int ncol = pre_n[nj];
     if (!small.empty())
       launch(PROF_EIG, [&] {
         syev_tridiag_kernel<1><<<unsigned(small.size()), SYEV_THREADS, smem1, st_>>>(dj, dsmall, maxn);
@@ -1461,13 +1257,115 @@ class CudaExec : public Exec {
                               static_cast<const int*>(dbig), maxn));
       });
     launch(PROF_EIG, [&] { syev_qform_kernel<<<unsigned((ncol + 7) / 8), 256, 0, st_>>>(dj, dpn, nj); });
-    launch(PROF_EIG, [&] { syev_ql_kernel<<<unsigned(nj), 32, smem3, st_>>>(dj, maxn, err_); });
-    launch(PROF_EIG, [&] { syev_rot_kernel<<<unsigned((nslab + 7) / 8), 256, 0, st_>>>(dj, dps, nj); });
+    // 3. T = V diag(d) V^T by divide and conquer: the blocks are halved until they
+    // have at most DC_LEAF rows; a merge runs once both halves are solved, so the
+    // merges go level by level (by the height of their subtree) over all matrices
+    std::vector<DcLeaf> leaves;
+    std::vector<std::vector<DcMerge>> levels;
+    for (int j = 0; j < nj; ++j) {
+      const SyevJob& jb = jobs[j];
+      std::function<int(int, int)> split = [&](int o, int sz) -> int {
+        if (sz <= DC_LEAF) {
+          leaves.push_back(DcLeaf{jb.d, jb.e, jb.A, jb.n, o, sz, 0});
+          return 0;
+        }
+        const int s1 = sz / 2;
+        const int h = std::max(split(o, s1), split(o + s1, sz - s1)) + 1;
+        if (int(levels.size()) < h) levels.resize(size_t(h));
+        DcMerge mg{};
+        mg.d = jb.d;
+        mg.e = jb.e;
+        mg.Z = jb.A;
+        mg.n = jb.n;
+        mg.o = o;
+        mg.s1 = s1;
+        mg.s = sz;
+        levels[size_t(h - 1)].push_back(mg);
+        return h;
+      };
+      split(0, jb.n);
+    }
+    DcLeaf* dl = upload(leaves);
+    launch(PROF_EIG, [&] { launch_dc_leaves(dl, int(leaves.size()), err_, st_); });
+    std::vector<void*> scratch;
+    for (auto& lv : levels) {
+      // scratch per merge: doubles 8 s + 2 s^2 + 2, ints 5 s + 4 (16-byte aligned parts)
+      int64_t nd = 0, ni = 0;
+      for (const DcMerge& mg : lv) {
+        nd += up2(8 * int64_t(mg.s) + 2) + 2 * up2(int64_t(mg.s) * mg.s);
+        ni += up4(5 * int64_t(mg.s) + 4);
+      }
+      double* sd = static_cast<double*>(alloc(sizeof(double) * size_t(nd)));
+      int* si = static_cast<int*>(alloc(sizeof(int) * size_t(ni)));
+      scratch.push_back(sd);
+      scratch.push_back(si);
+      std::vector<int> ps(lv.size() + 1, 0), pt(lv.size() + 1, 0);
+      int64_t od = 0, oi = 0;
+      for (size_t i = 0; i < lv.size(); ++i) {
+        DcMerge& mg = lv[i];
+        const int64_t s = mg.s;
+        double* p = sd + od;
+        mg.ds = p;
+        mg.zs = p + s;
+        mg.dk = p + 2 * s;
+        mg.zk = p + 3 * s;
+        mg.tau = p + 4 * s;
+        mg.zh = p + 5 * s;
+        mg.gc = p + 6 * s;
+        mg.gs = p + 7 * s;
+        mg.rho = p + 8 * s;
+        p += up2(8 * s + 2);
+        mg.Qp = p;
+        p += up2(s * s);
+        mg.U = p;
+        od += up2(8 * s + 2) + 2 * up2(s * s);
+        int* q = si + oi;
+        mg.perm = q;
+        mg.ndp = q + s;
+        mg.org = q + 2 * s;
+        mg.gp = q + 3 * s;
+        mg.cnt = q + 5 * s;
+        oi += up4(5 * s + 4);
+        const int nt = int((s + 63) / 64);
+        ps[i + 1] = ps[i] + int(s);
+        pt[i + 1] = pt[i] + nt * nt;
+      }
+      DcMerge* dm = upload(lv);
+      int* dps = upload(ps);
+      int* dpt = upload(pt);
+      launch(PROF_EIG, [&] {
+        launch_dc_merges(dm, int(lv.size()), dps, ps.back(), dpt, pt.back(), st_);
+      });
+      release(dm);
+      release(dps);
+      release(dpt);
+    }
+    // 4. W = Q V (column-major both: as row-major arrays W^T = V^T Q^T), into U
+    {
+      std::vector<GemmProb> P;
+      std::vector<GemmSeg> S;
+      for (const SyevJob& jb : jobs) {
+        GemmProb q;
+        q.C = jb.U;
+        q.ldc = jb.n;
+        q.M = jb.n;
+        q.N = jb.n;
+        q.alpha = 1.0;
+        q.accumulate = 0;
+        q.s0 = int(S.size());
+        S.push_back(GemmSeg{jb.A, jb.Zc, jb.n, jb.n, jb.n, 0, 0});
+        q.s1 = int(S.size());
+        P.push_back(q);
+      }
+      gemm(P, S);
+    }
+    // 5. order
     launch(PROF_EIG, [&] { syev_sort_kernel<<<unsigned((ncol + 255) / 256), 256, 0, st_>>>(dj, dpn, nj); });
     launch(PROF_EIG, [&] { syev_perm_kernel<<<unsigned(ncol), 128, 0, st_>>>(dj, dpn, nj); });
+    for (void* p : scratch) release(p);
+    release(dl);
     release(dj);
     release(dpn);
-    release(dps);
     release(dsmall);
     release(dbig);
     release(dw);
