@@ -24,21 +24,22 @@ struct DcMerge {
   const double* e;
   double* Z;
   int n, o, s1, s;
-  // scratch (device, owned by the caller): doubles 8 s + 2 s^2, ints 4 s + 4
+  // scratch (device, owned by the caller): doubles 8 s + 2 + 2 s^2, ints 5 s + 4
   double* ds;   // s: sorted diagonal (after the deflation rotations)
   double* zs;   // s: sorted z (after the deflation rotations)
   double* dk;   // s: the k non-deflated ds, ascending
   double* zk;   // s: their z
   double* tau;  // s: secular roots as offsets from their origin pole
   double* zh;   // s: z recomputed from the roots (Gu-Eisenstat)
-  double* gc;   // s: deflation rotations (cosine, sine)
+  double* gc;   // s: deflation rotations (cosine, sine); first z and d of the two blocks
   double* gs;
   double* Qp;   // s x s column-major: the two blocks' eigenvectors, sorted and rotated
   double* U;    // k x k column-major: eigenvectors of diag(dk) + rho zk zk^T
   int* perm;    // s: sorted position -> column of the two blocks
   int* ndp;     // s: j-th non-deflated sorted position
   int* org;     // s: origin pole of root j
-  int* gp;      // s: deflation rotation pairs (p in low 16... stored as two ints)
+  int* gp;      // 2 s: slot 2 q the q-th deflation rotation's pair p | i << 16, slot 2 i + 1
+                //      pole i's flag (-1 deflated, 0 kept)
   int* cnt;     // 4: k, number of deflation rotations
   double* rho;  // 1: the rank-one weight rho ||z||^2
 };
