@@ -354,8 +354,8 @@ __global__ void __maxnreg__(96)
     // control word and copies the operand slabs: the slab of a 128-row operand
     // tile is contiguous in HBM (blocked split layout), so a stage is one bulk copy
     // for A and one for B (one per 8-row group for gathered A rows), completing on
-    // the stage's transaction count.  The next tiles' records are prefetched one
-    // and two tiles ahead.
+    // the stage's transaction count.  The next tile's records are prefetched one
+    // tile ahead.
     int step = 0, tcount = 0;
     bool stop = false;
     // CTA c starts with tile c.  With a counter (next_tile), each next tile is
