@@ -674,7 +674,7 @@ def batched_bench(args, B, I):
     pp = [p.data_ptr() for p in psis]
     sp = [s.data_ptr() for s in sigs]
     batch = B.Batch(ds, bonds)
-    sched = batch.schedule()
+    sched = batch.tuning()   # tile order and tile width per launch, with every candidate's time
 
     def timed(fn, k):
         for _ in range(3):

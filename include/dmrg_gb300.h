@@ -397,6 +397,15 @@ dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out14);
  */
 typedef struct dmrg_batch dmrg_batch;
 dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int32_t* bonds, dmrg_batch** out);
+/* The same with the tile shape of the merged launches fixed (an implementation
+ * parameter; the paper has no counterpart): tile_width = 0 lets
+ * dmrg_batch_create's autotuner choose the tile width (MMA N) of stages 1 and 2
+ * among 128 and 64 together with the order; 64 or 128 fixes it for all three
+ * launches (orders still tuned); anything else is DMRG_ERR_ARG.  Every
+ * width computes each element of sigma with the same products in the same
+ * order. */
+dmrg_status dmrg_batch_create_ex(int32_t n, dmrg_handle* const* handles, const int32_t* bonds, int32_t tile_width,
+                                 dmrg_batch** out);
 dmrg_status dmrg_batch_sigma(dmrg_batch* b, const double* const* psi_dev, double* const* sigma_dev,
                              int32_t use_graph);
 /* Tile schedule of the batch's merged launches (an implementation parameter;
@@ -408,6 +417,12 @@ dmrg_status dmrg_batch_sigma(dmrg_batch* b, const double* const* psi_dev, double
  * ms9[3k + o] (host, may be NULL) = measured milliseconds of order o for stage k
  * (0 where not timed).  The order changes only the time, never the result. */
 dmrg_status dmrg_batch_schedule(dmrg_batch* b, int32_t* order3, float* ms9);
+/* The autotuner's full record: order3[k] and width3[k] (tile width, MMA N) chosen
+ * for launch k (0 local term, 1 stage 1, 2 stage 2); ms18[6k + 2o + w] (host, may
+ * be NULL) = measured milliseconds of order o at width 128 (w = 0) or 64 (w = 1),
+ * 0 where not timed.  dmrg_batch_schedule's ms9 holds the times at the chosen
+ * width. */
+dmrg_status dmrg_batch_tuning(dmrg_batch* b, int32_t* order3, int32_t* width3, float* ms18);
 void dmrg_batch_destroy(dmrg_batch* b);
 
 void dmrg_destroy(dmrg_handle* h);

@@ -22,7 +22,8 @@ SYMBOLS = ["dmrg_build_ops", "dmrg_load_site", "dmrg_prepare", "dmrg_layout", "d
            "dmrg_sweep_state", "dmrg_set_state", "dmrg_expectation", "dmrg_orbital_gradient", "dmrg_term_work",
            "dmrg_term_partition", "dmrg_sigma_subset", "dmrg_graph_replays", "dmrg_two_site_rotate",
            "dmrg_half_renyi", "dmrg_eigh_batch", "dmrg_mode_step", "dmrg_get_integrals", "dmrg_mode_log", "dmrg_stats",
-           "dmrg_plan_paths", "dmrg_profile", "dmrg_batch_create", "dmrg_batch_sigma", "dmrg_batch_schedule", "dmrg_batch_destroy", "dmrg_destroy",
+           "dmrg_plan_paths", "dmrg_profile", "dmrg_batch_create", "dmrg_batch_create_ex", "dmrg_batch_sigma", "dmrg_batch_schedule",
+           "dmrg_batch_tuning", "dmrg_batch_destroy", "dmrg_destroy",
            "dmrg_last_error"]
 SWEEP_PHASES = ["tables", "diag_h", "svd", "ren", "stvec"]
 PROFILE_CLASSES = ["gemm_f64", "kron", "vector", "eigen", "gemm_bf16x", "split", "gemm_bf16x_stage1"]
@@ -88,7 +89,9 @@ def load_library(path: str | None = None):
         "dmrg_profile": ([vp, i32, dp], ctypes.c_int),
         "dmrg_batch_create": ([i32, ctypes.POINTER(vp), ip, ctypes.POINTER(vp)], ctypes.c_int),
         "dmrg_batch_sigma": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32], ctypes.c_int),
+        "dmrg_batch_create_ex": ([i32, ctypes.POINTER(vp), ip, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "dmrg_batch_schedule": ([vp, ip, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "dmrg_batch_tuning": ([vp, ip, ip, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "dmrg_batch_destroy": ([vp], None),
         "dmrg_destroy": ([vp], None),
         "dmrg_last_error": ([], ctypes.c_char_p),
@@ -344,15 +347,16 @@ class Dmrg:
 class Batch:
     """Split-BF16 sigma steps of several prepared problems in shared grouped launches."""
 
-    def __init__(self, problems, bonds):
+    def __init__(self, problems, bonds, tile_width=0):
+        """tile_width 0: the autotuner picks the tile width (128 or 64) with the order; 64 or 128 fixes it."""
         self.problems = list(problems)   # keeps the handles alive while the batch lives
         self.lib = self.problems[0].lib
         n = len(self.problems)
         hs = (ctypes.c_void_p * n)(*[p.h.value for p in self.problems])
         bs = np.ascontiguousarray(bonds, dtype=np.int32)
         b = ctypes.c_void_p()
-        self._check(self.lib.dmrg_batch_create(n, hs, bs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                               ctypes.byref(b)))
+        self._check(self.lib.dmrg_batch_create_ex(n, hs, bs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                  int(tile_width), ctypes.byref(b)))
         self.b = b
 
     def _check(self, st):
@@ -371,6 +375,16 @@ class Batch:
         ms = (ctypes.c_float * 9)()
         self._check(self.lib.dmrg_batch_schedule(self.b, o, ms))
         return {"order": list(o), "ms": [list(ms[3 * k:3 * k + 3]) for k in range(3)]}
+
+    def tuning(self):
+        """Order and tile width chosen per launch (local term, stage 1, stage 2); ms[k][o][w] of order o at
+        width 128 (w = 0) or 64 (w = 1), 0 where not timed."""
+        o = (ctypes.c_int32 * 3)()
+        w = (ctypes.c_int32 * 3)()
+        ms = (ctypes.c_float * 18)()
+        self._check(self.lib.dmrg_batch_tuning(self.b, o, w, ms))
+        return {"order": list(o), "width": list(w),
+                "ms": [[[ms[6 * k + 2 * oo + ww] for ww in range(2)] for oo in range(3)] for k in range(3)]}
 
     def close(self):
         if getattr(self, "b", None):

@@ -36,7 +36,8 @@ struct dmrg_batch {
   cudaGraphExec_t gexec = nullptr;
   bool dead = false;   // one of its handles was destroyed: plans released
   int order[3] = {0, 0, 0};                  // chosen tile order: local term, stage 1, stage 2
-  float ms[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // measured ms per candidate order
+  int width[3] = {128, 128, 128};            // chosen tile width (MMA N) of the same launches
+  float ms[3][6] = {};                       // measured ms per candidate: [2 order + (width == 64)]
 };
 
 namespace {
@@ -86,32 +87,41 @@ Merged merge(const std::vector<std::pair<dmrg::Exec*, int>>& parts) {
   return m;
 }
 
-// Autotuner of the merged launch's tile schedule: every candidate order is built
-// and timed on the GPU (CUDA events, one warm-up run), the fastest is kept.  All
-// orders compute every output tile identically, so the choice changes only the
-// time.  Running a plan here is harmless: it writes only the handles' own
-// intermediate buffers, which every sigma step rewrites before reading.
-int build_tuned(dmrg::Exec* owner, const Merged& m, bool tune, int* order_out, float* ms_out) {
+// Autotuner of the merged launch's tile schedule and tile shape: every candidate
+// (three orders x tile widths 128 and 64, or the one width the caller fixed) is
+// built and timed on the GPU (CUDA events, one warm-up run), the fastest is kept.
+// All candidates compute every output element with the same products in the same
+// order, so the choice changes only the time.  Running a plan here is harmless:
+// it writes only the handles' own intermediate buffers, which every sigma step
+// rewrites before reading.  ms_out[2 order + (width == 64)] receives the times.
+int build_tuned(dmrg::Exec* owner, const Merged& m, bool tune, int fixed_width, int* order_out, int* width_out,
+                float* ms_out) {
   if (m.P.empty()) return -1;
+  const int w0 = fixed_width > 0 ? fixed_width : 128;
   if (!tune) {
     *order_out = 0;
-    return owner->mix_plan_ordered(m.P, m.S, m.bcol, m.ccol, m.acol, 0);
+    *width_out = w0;
+    return owner->mix_plan_ordered(m.P, m.S, m.bcol, m.ccol, m.acol, 0, w0);
   }
+  std::vector<int> widths{w0};
+  if (fixed_width <= 0) widths.push_back(64);
   int best = -1;
   float best_ms = 0.f;
-  for (int order = 0; order < 3; ++order) {
-    const int id = owner->mix_plan_ordered(m.P, m.S, m.bcol, m.ccol, m.acol, order);
-    const float ms = owner->mix_time(id, 2);
-    ms_out[order] = ms;
-    if (best < 0 || ms < best_ms) {
-      if (best >= 0) owner->mix_plan_free(best);
-      best = id;
-      best_ms = ms;
-      *order_out = order;
-    } else {
-      owner->mix_plan_free(id);
+  for (int order = 0; order < 3; ++order)
+    for (int w : widths) {
+      const int id = owner->mix_plan_ordered(m.P, m.S, m.bcol, m.ccol, m.acol, order, w);
+      const float ms = owner->mix_time(id, 2);
+      ms_out[2 * order + (w == 64 ? 1 : 0)] = ms;
+      if (best < 0 || ms < best_ms) {
+        if (best >= 0) owner->mix_plan_free(best);
+        best = id;
+        best_ms = ms;
+        *order_out = order;
+        *width_out = w;
+      } else {
+        owner->mix_plan_free(id);
+      }
     }
-  }
   return best;
 }
 
@@ -159,8 +169,15 @@ void issue(dmrg_batch* b, const double* const* psi, double* const* sig) {
 extern "C" {
 
 dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int32_t* bonds, dmrg_batch** out) {
+  return dmrg_batch_create_ex(n, handles, bonds, 0, out);
+}
+
+dmrg_status dmrg_batch_create_ex(int32_t n, dmrg_handle* const* handles, const int32_t* bonds, int32_t tile_width,
+                                 dmrg_batch** out) {
   return guard([&]() -> dmrg_status {
     if (!out || n <= 0 || !handles || !bonds) return fail(DMRG_ERR_ARG, "bad arguments");
+    if (tile_width != 0 && tile_width != 64 && tile_width != 128)
+      return fail(DMRG_ERR_ARG, "tile_width must be 0 (tuned), 64 or 128");
     *out = nullptr;
     auto b = std::make_unique<dmrg_batch>();
     for (int i = 0; i < n; ++i) {
@@ -190,9 +207,9 @@ dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int3
     }
     const bool tune = !b->owner->profiling();   // timing runs would pollute the caller's kernel profile
     try {
-      b->plan_hl = build_tuned(b->owner, merge(hl), false, &b->order[0], b->ms[0]);
-      b->plan1 = build_tuned(b->owner, merge(p1), tune, &b->order[1], b->ms[1]);
-      b->plan2 = build_tuned(b->owner, merge(p2), tune, &b->order[2], b->ms[2]);
+      b->plan_hl = build_tuned(b->owner, merge(hl), false, tile_width, &b->order[0], &b->width[0], b->ms[0]);
+      b->plan1 = build_tuned(b->owner, merge(p1), tune, tile_width, &b->order[1], &b->width[1], b->ms[1]);
+      b->plan2 = build_tuned(b->owner, merge(p2), tune, tile_width, &b->order[2], &b->width[2], b->ms[2]);
       b->owner->sync();
     } catch (...) {
       for (int id : {b->plan_hl, b->plan1, b->plan2})
@@ -266,7 +283,20 @@ dmrg_status dmrg_batch_schedule(dmrg_batch* b, int32_t* order3, float* ms9) {
     for (int k = 0; k < 3; ++k) {
       order3[k] = b->order[k];
       if (ms9)
-        for (int o = 0; o < 3; ++o) ms9[3 * k + o] = b->ms[k][o];
+        for (int o = 0; o < 3; ++o) ms9[3 * k + o] = b->ms[k][2 * o + (b->width[k] == 64 ? 1 : 0)];
+    }
+    return DMRG_OK;
+  });
+}
+
+dmrg_status dmrg_batch_tuning(dmrg_batch* b, int32_t* order3, int32_t* width3, float* ms18) {
+  return guard([&]() -> dmrg_status {
+    if (!b || !order3 || !width3) return fail(DMRG_ERR_ARG, "null argument");
+    for (int k = 0; k < 3; ++k) {
+      order3[k] = b->order[k];
+      width3[k] = b->width[k];
+      if (ms18)
+        for (int c = 0; c < 6; ++c) ms18[6 * k + c] = b->ms[k][c];
     }
     return DMRG_OK;
   });

@@ -186,12 +186,14 @@ class Exec {
   virtual int mix_plan_g(const std::vector<MixProb>& p, const std::vector<MixSeg>& s,
                          const std::vector<int64_t>& bcol, const std::vector<int64_t>& ccol,
                          const std::vector<float>& acol) = 0;
-  // the same with a tile schedule: order 0 = longest tile first over the whole
-  // list (the default), 1 = problems in the given order, each problem's tiles
-  // together, 2 = problems by decreasing total work, each problem's tiles together
+  // the same with a tile schedule and shape: order 0 = longest tile first over the
+  // whole list (the default), 1 = problems in the given order, each problem's tiles
+  // together, 2 = problems by decreasing total work, each problem's tiles together;
+  // width = tile width (MMA N) of every tile: 128 (the default), 64 or 32.  Every
+  // choice computes each output element with the same products in the same order
   virtual int mix_plan_ordered(const std::vector<MixProb>& p, const std::vector<MixSeg>& s,
                                const std::vector<int64_t>& bcol, const std::vector<int64_t>& ccol,
-                               const std::vector<float>& acol, int order) = 0;
+                               const std::vector<float>& acol, int order, int width) = 0;
   virtual void mix_run(int plan) = 0;
   // milliseconds per run of a plan (CUDA events on the stream, after one warm-up run)
   virtual float mix_time(int plan, int reps) = 0;

@@ -937,6 +937,7 @@ class CudaExec : public Exec {
     float* acol = nullptr;
     int* next_tile = nullptr;
     int ntiles = 0;
+    int width = MIX_TN;
     int cls = PROF_MIXED;
     bool live = false;
     MixPlanHost host;
@@ -955,11 +956,13 @@ class CudaExec : public Exec {
   }
   int mix_plan_g(const std::vector<MixProb>& p, const std::vector<MixSeg>& s, const std::vector<int64_t>& bcol,
                  const std::vector<int64_t>& ccol, const std::vector<float>& acol) override {
-    return mix_plan_ordered(p, s, bcol, ccol, acol, 0);
+    return mix_plan_ordered(p, s, bcol, ccol, acol, 0, MIX_TN);
   }
   int mix_plan_ordered(const std::vector<MixProb>& p, const std::vector<MixSeg>& s, const std::vector<int64_t>& bcol,
-                       const std::vector<int64_t>& ccol, const std::vector<float>& acol, int order) override {
+                       const std::vector<int64_t>& ccol, const std::vector<float>& acol, int order,
+                       int width) override {
     if (order < 0 || order > 2) throw std::runtime_error("mix_plan: unknown tile order");
+    if (!mix_width_ok(width)) throw std::runtime_error("mix_plan: tile width must be 32, 64 or 128");
     for (const MixSeg& g : s) {
       // blocked split matrices are built of 128-byte core-matrix pairs: every
       // bulk copy source is 16-byte aligned when the matrix base is
@@ -986,7 +989,7 @@ class CudaExec : public Exec {
       int64_t w = 1;
       for (int q = p[i].s0; q < p[i].s1; ++q) w += (s[q].K + 31) / 32;
       for (int m0 = 0; m0 < p[i].M; m0 += MIX_TM)
-        for (int n0 = 0; n0 < p[i].N; n0 += MIX_TN) {
+        for (int n0 = 0; n0 < p[i].N; n0 += width) {
           tiles.push_back(MixTile{int(i), m0, n0, int(w - 1)});
           work.push_back(w);
         }
@@ -1014,6 +1017,7 @@ class CudaExec : public Exec {
     }
     MixPlanD pl;
     pl.ntiles = int(tiles.size());
+    pl.width = width;
     pl.tiles = upload(tiles);
     pl.probs = upload(p);
     pl.segs = upload(s);
@@ -1039,7 +1043,8 @@ class CudaExec : public Exec {
       // tiles handed out through the counter where they are long (the K-concatenated
       // products of stage 2); in fixed strides where they are short (stage 1)
       int* nt = pl.cls == PROF_MIXED ? pl.next_tile : nullptr;
-      launch_mixed_gemm(pl.tiles, pl.ntiles, pl.probs, pl.segs, pl.bcol, pl.ccol, pl.acol, err_, nt, nsm_, st_);
+      launch_mixed_gemm(pl.tiles, pl.ntiles, pl.probs, pl.segs, pl.bcol, pl.ccol, pl.acol, err_, nt, pl.width, nsm_,
+                        st_);
     });
   }
   void mix_plan_free(int id) override { mix_free(id); }

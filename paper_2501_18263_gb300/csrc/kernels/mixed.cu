@@ -251,7 +251,7 @@ __global__ void __maxnreg__(96)
     mixed_gemm_kernel(const MixTile* __restrict__ tiles, int ntiles, const MixProb* __restrict__ probs,
                       const MixSeg* __restrict__ segs, const int64_t* __restrict__ bcol,
                       const int64_t* __restrict__ ccol, const float* __restrict__ acol, int* err,
-                      int* next_tile) {
+                      int* next_tile, int tn) {
   extern __shared__ __align__(1024) uint8_t smem[];
   TileSlot* slots = reinterpret_cast<TileSlot*>(smem + SLOT_OFF);
   StageInfo* info = reinterpret_cast<StageInfo*>(smem + INFO_OFF);
@@ -392,7 +392,7 @@ __global__ void __maxnreg__(96)
         stop = true;
         break;
       }
-      const int Nt = min(MIX_TN, p.N - tl.n0);
+      const int Nt = min(tn, p.N - tl.n0);
       if (lane == 0) {
         TileSlot& sl = slots[slot];
         sl.Chi = p.Chi;
@@ -419,7 +419,11 @@ __global__ void __maxnreg__(96)
         }
       }
       const int hA = min(MIX_TM, ((p.M + 7) & ~7) - tl.m0);   // rows of A in the tile (multiple of 8)
-      const int hB = min(MIX_TN, ((p.N + 7) & ~7) - tl.n0);
+      const int hB = min(tn, ((p.N + 7) & ~7) - tl.n0);
+      // a tile narrower than 128 starts inside a 128-row block of B: its rows are a
+      // contiguous run at row offset n0 % 128 of each slab, whose stride is set by
+      // the block's height
+      const int hBk = min(MIX_TN, ((p.N + 7) & ~7) - (tl.n0 & ~127));
       const int64_t u0 = p.cm0 / 8 + (tl.m0 >> 3);            // first gathered unit of the tile
       const int nmma = (Nt + 15) & ~15;
       int left = tl.nsteps;
@@ -427,7 +431,7 @@ __global__ void __maxnreg__(96)
         const MixSeg g = (s == p.s0) ? gf : segs[s];
         const int64_t Kt = (g.K + 31) & ~31;
         const uint16_t* Ab = g.A + int64_t(tl.m0 >> 7) * 384 * Kt;
-        const uint16_t* Bb = g.B + int64_t(tl.n0 >> 7) * 384 * Kt;
+        const uint16_t* Bb = g.B + int64_t(tl.n0 >> 7) * 384 * Kt + (tl.n0 & 127) * 96;
         for (int k0 = 0; k0 < g.K; k0 += BK, ++step) {
           const int st = step % STAGES;
           if (step >= STAGES && !mbar_wait_warp(empty(st), ((step / STAGES) - 1) & 1, abort_flag, err, 2)) {
@@ -441,7 +445,7 @@ __global__ void __maxnreg__(96)
             info[st] = StageInfo{(g.K - k0 > 16) ? 2 : 1, last ? 1 : 0, nmma, 0};
             mbar_expect_tx(full(st), uint32_t(hA + hB) * 192u);
             if (p.mode != 3) bulk_copy(base, Ab + sl * 96 * hA, uint32_t(hA) * 192u, full(st));
-            bulk_copy(base + OPER_BYTES, Bb + sl * 96 * hB, uint32_t(hB) * 192u, full(st));
+            bulk_copy(base + OPER_BYTES, Bb + sl * 96 * hBk, uint32_t(hB) * 192u, full(st));
           }
           __syncwarp();   // the transaction count is raised before the gathered copies
           if (p.mode == 3 && lane < (hA >> 3)) {
@@ -702,7 +706,7 @@ __global__ void df_to_f64_kernel(const float* __restrict__ hi, const float* __re
 
 void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, const MixSeg* segs,
                        const int64_t* bcol, const int64_t* ccol, const float* acol, int* err, int* next_tile,
-                       int nsm, cudaStream_t st) {
+                       int tn, int nsm, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(mixed_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -711,7 +715,8 @@ void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, c
   const int grid = ntiles < nsm ? ntiles : nsm;
   if (ntiles > 0) {
     if (next_tile) cudaMemsetAsync(next_tile, 0, sizeof(int), st);
-    mixed_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(tiles, ntiles, probs, segs, bcol, ccol, acol, err, next_tile);
+    mixed_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(tiles, ntiles, probs, segs, bcol, ccol, acol, err, next_tile,
+                                                          tn);
   }
 }
 

@@ -65,6 +65,11 @@ def test_batch_argument_errors_without_a_device(lib):
     assert L.dmrg_batch_create(1, hs, bonds, ctypes.byref(b)) == binding.ERR_ARG
     assert b"null handle" in L.dmrg_last_error()
     assert L.dmrg_batch_sigma(None, None, None, 0) == binding.ERR_ARG
+    assert L.dmrg_batch_create_ex(1, hs, bonds, 96, ctypes.byref(b)) == binding.ERR_ARG
+    assert b"tile_width" in L.dmrg_last_error()
+    assert L.dmrg_batch_create_ex(1, hs, bonds, 64, ctypes.byref(b)) == binding.ERR_ARG   # null handle
+    o3, w3 = (ctypes.c_int32 * 3)(), (ctypes.c_int32 * 3)()
+    assert L.dmrg_batch_tuning(None, o3, w3, None) == binding.ERR_ARG
     L.dmrg_batch_destroy(None)
 
 

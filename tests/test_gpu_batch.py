@@ -50,6 +50,13 @@ def test_batched_sigma_is_bit_identical_to_single_problem_sigma():
     sch = batch.schedule()          # tile orders picked by timing every candidate
     assert all(0 <= o <= 2 for o in sch["order"])
     assert min(sch["ms"][1]) > 0 and min(sch["ms"][2]) > 0
+    tu = batch.tuning()             # ... and tile widths: three orders x widths 128 and 64 per stage
+    assert tu["order"] == sch["order"] and tu["width"][0] == 128
+    for k in (1, 2):
+        assert tu["width"][k] in (64, 128)
+        assert min(min(m) for m in tu["ms"][k]) > 0
+        best = min(min(m) for m in tu["ms"][k])
+        assert tu["ms"][k][tu["order"][k]][0 if tu["width"][k] == 128 else 1] == best
     outs = [torch.full_like(p, float("nan")) for p in psis]
     batch.sigma([p.data_ptr() for p in psis], [o.data_ptr() for o in outs], graph=False)
     for o, r in zip(outs, refs):
@@ -68,6 +75,28 @@ def test_batched_sigma_is_bit_identical_to_single_problem_sigma():
                 refs.append(r)
         batch.sigma([p.data_ptr() for p in psis], [o.data_ptr() for o in outs2], graph=True)
         for o, r in zip(outs2, refs):
+            assert bool((o == r).all())
+    batch.close()
+    for d in ds:
+        d.close()
+
+
+@pytest.mark.parametrize("width", [64, 128])
+def test_every_tile_width_gives_the_single_problem_sigma_bit_for_bit(width):
+    """The tile width is a shape choice of the grouped launch only: tiles 64 columns
+    wide start inside the 128-row blocks of the B operands and split each output
+    block differently, yet every element of sigma is the same sum of the same
+    products, eagerly and from the captured graph."""
+    import torch
+    stream = torch.cuda.Stream()
+    ds, bonds, psis, refs = _setup(stream)
+    batch = B.Batch(ds, bonds, tile_width=width)
+    tu = batch.tuning()
+    assert tu["width"] == [width] * 3
+    for graph in (False, True):
+        outs = [torch.full_like(p, float("nan")) for p in psis]
+        batch.sigma([p.data_ptr() for p in psis], [o.data_ptr() for o in outs], graph=graph)
+        for o, r in zip(outs, refs):
             assert bool((o == r).all())
     batch.close()
     for d in ds:
