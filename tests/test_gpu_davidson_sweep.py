@@ -46,6 +46,24 @@ def test_truncated_sweeps_are_variational_and_monotone_in_D():
     assert es[0] >= es[1] - 1e-9 and es[1] >= es[2] - 1e-9
 
 
+def test_eight_orbital_workload_at_D64_is_variational_and_D256_is_exact():
+    """The L = 8, 4a+4b workload with its own seed (1) at D = 64 and at the full D = 256.
+    The ground state's 4|4 cut carries 240 nonzero Schmidt values, the 64 largest leaving
+    about 7.5e-4 of the weight, so D = 64 truncates: its energy lies above full CI and
+    below D = 32, while D = 256 keeps the whole basis and equals full CI."""
+    L, na, nb = 8, 4, 4
+    t, v = I.synthetic_integrals(L, 1)
+    efci = O.fci_lowest(t, v, na, nb)[0][0]
+    e = {}
+    for D in (32, 64, 256):
+        d = B.Dmrg(t, v, na, nb, D=D, seed=1, stream=stream())
+        e[D] = d.sweep(4, [D] * 4, tol=1e-9, max_iter=400)[-1]
+        d.close()
+    assert abs(e[256] - efci) < 1e-8
+    assert e[64] > efci + 1e-7
+    assert e[64] <= e[32] + 1e-9
+
+
 def test_orbital_order_is_irrelevant_without_truncation():
     """Sec. 2.2: without truncation the mode order does not change the energy."""
     L, na, nb = 6, 3, 3
