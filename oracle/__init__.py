@@ -21,6 +21,10 @@ Contents
   * expm_skew / rotate_integrals / orbital_gradient: orbital rotations
     U = exp(kappa) of the integrals (Sec. 2.2) and the generalised-Fock gradient
     dE/dkappa from the one- and two-particle density matrices.
+  * rotate_state / half_renyi_cut: a determinant expansion re-expressed in rotated
+    orbitals (exp(-K) of the one-body generator by a scaled-and-squared Taylor series) and the
+    half-Renyi entropy of a cut from the singular values across it (the quantities
+    of the mode-optimisation step, Sec. 2.2).
 """
 from __future__ import annotations
 
