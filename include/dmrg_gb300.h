@@ -28,6 +28,11 @@
  *     host pointers are ordinary CPU memory.  The caller owns every buffer it
  *     passes; the library owns everything it allocates and frees it in
  *     dmrg_destroy.
+ *   - A handle lives on the CUDA device that was current at dmrg_build_ops.
+ *     Every call on a handle (or on a batch of handles) makes that device
+ *     current for its duration and restores the caller's current device before
+ *     it returns; dmrg_sigma_host_noalloc instead requires the handle's device
+ *     to be current.
  *
  * Errors: every call returns a dmrg_status; nothing aborts or throws across
  * the ABI.  dmrg_last_error() gives a message for the calling thread.  After

@@ -27,6 +27,7 @@ struct dmrg_batch {
   std::vector<int> bond;
   std::vector<uint64_t> gen;
   dmrg::Exec* owner = nullptr;   // executor of the first handle: holds the merged plans
+  int device = -1;               // the handles' CUDA device (made current by every batch call)
   cudaStream_t st = nullptr;
   int plan_hl = -1, plan1 = -1, plan2 = -1;
   // captured graph and the buffers it was captured with
@@ -174,7 +175,8 @@ dmrg_status dmrg_batch_create(int32_t n, dmrg_handle* const* handles, const int3
 
 dmrg_status dmrg_batch_create_ex(int32_t n, dmrg_handle* const* handles, const int32_t* bonds, int32_t tile_width,
                                  dmrg_batch** out) {
-  return guard([&]() -> dmrg_status {
+  const int dev = (n > 0 && handles && handles[0]) ? handles[0]->device : -1;
+  return dmrg_internal_guard_on(dev, [&]() -> dmrg_status {
     if (!out || n <= 0 || !handles || !bonds) return fail(DMRG_ERR_ARG, "bad arguments");
     if (tile_width != 0 && tile_width != 64 && tile_width != 128)
       return fail(DMRG_ERR_ARG, "tile_width must be 0 (tuned), 64 or 128");
@@ -198,6 +200,7 @@ dmrg_status dmrg_batch_create_ex(int32_t n, dmrg_handle* const* handles, const i
       b->gen.push_back(h->eng->plan_generation());
     }
     b->owner = handles[0]->eng->exec();
+    b->device = handles[0]->device;
     b->st = static_cast<cudaStream_t>(b->owner->stream());
     std::vector<std::pair<dmrg::Exec*, int>> hl, p1, p2;
     for (dmrg_handle* h : b->h) {
@@ -224,7 +227,7 @@ dmrg_status dmrg_batch_create_ex(int32_t n, dmrg_handle* const* handles, const i
 
 dmrg_status dmrg_batch_sigma(dmrg_batch* b, const double* const* psi_dev, double* const* sigma_dev,
                              int32_t use_graph) {
-  return guard([&]() -> dmrg_status {
+  return dmrg_internal_guard_on(b ? b->device : -1, [&]() -> dmrg_status {
     if (!b || !psi_dev || !sigma_dev) return fail(DMRG_ERR_ARG, "null argument");
     if (b->dead) return fail(DMRG_ERR_STATE, "a handle of the batch was destroyed; destroy the batch");
     const size_t n = b->h.size();
@@ -305,6 +308,7 @@ dmrg_status dmrg_batch_tuning(dmrg_batch* b, int32_t* order3, int32_t* width3, f
 void dmrg_batch_destroy(dmrg_batch* b) {
   if (!b) return;
   try {
+    DmrgDeviceGuard dg(b->dead ? -1 : b->device);   // the merged plans live on the handles' device
     retire(b);
   } catch (...) {
   }

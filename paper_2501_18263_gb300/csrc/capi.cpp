@@ -22,6 +22,13 @@ dmrg_status guard(F&& f) {
   return dmrg_internal_guard(std::forward<F>(f));
 }
 
+// entry points on a handle run with the handle's device current (the device that
+// was current at dmrg_build_ops); the caller's current device is restored on return
+template <class F>
+dmrg_status guard_h(dmrg_handle* h, F&& f) {
+  return dmrg_internal_guard_on(h ? h->device : -1, std::forward<F>(f));
+}
+
 bool finite(const double* p, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(p[i])) return false;
@@ -121,7 +128,7 @@ dmrg_status dmrg_build_ops(const dmrg_problem* p, void* stream, dmrg_handle** ou
 
 dmrg_status dmrg_load_site(dmrg_handle* h, int32_t site, int32_t side, int32_t n_sectors,
                            const int32_t* sectors, const double* data) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !sectors || !data || n_sectors <= 0) return fail(DMRG_ERR_ARG, "null argument");
     if (site < 0 || site >= h->L) return fail(DMRG_ERR_ARG, "site out of range");
     dmrg::Sectors s;
@@ -166,7 +173,7 @@ dmrg_status dmrg_load_site(dmrg_handle* h, int32_t site, int32_t side, int32_t n
 }
 
 dmrg_status dmrg_prepare(dmrg_handle* h, int32_t bond) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h) return fail(DMRG_ERR_ARG, "null handle");
     if (bond < 0 || bond > h->L - 2) return fail(DMRG_ERR_ARG, "bond out of range");
     if (!h->eng->left_buildable(bond)) return fail(DMRG_ERR_ARG, "left sites 0..bond-1 are not loaded");
@@ -181,7 +188,7 @@ dmrg_status dmrg_prepare(dmrg_handle* h, int32_t bond) {
 
 dmrg_status dmrg_layout(dmrg_handle* h, int32_t bond, int32_t* n_blocks, const int64_t** table,
                         int64_t* psi_size) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !n_blocks || !table) return fail(DMRG_ERR_ARG, "null argument");
     if (h->eng->bond() != bond) return fail(DMRG_ERR_ARG, "bond not prepared (call dmrg_prepare)");
     *n_blocks = int32_t(h->eng->layout().size() / 7);
@@ -192,7 +199,7 @@ dmrg_status dmrg_layout(dmrg_handle* h, int32_t bond, int32_t* n_blocks, const i
 }
 
 dmrg_status dmrg_sigma(dmrg_handle* h, int32_t bond, const double* psi, double* sig) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !psi || !sig) return fail(DMRG_ERR_ARG, "null argument");
     dmrg_status s = ensure_bond(h, bond);
     if (s != DMRG_OK) return s;
@@ -203,7 +210,7 @@ dmrg_status dmrg_sigma(dmrg_handle* h, int32_t bond, const double* psi, double* 
 }
 
 dmrg_status dmrg_sigma_ex(dmrg_handle* h, int32_t bond, const double* psi, double* sig, int32_t precision) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !psi || !sig) return fail(DMRG_ERR_ARG, "null argument");
     if (precision != DMRG_PREC_FP64 && precision != DMRG_PREC_MIXED_BF16) return fail(DMRG_ERR_ARG, "unknown precision");
     if (precision == DMRG_PREC_MIXED_BF16 && h->eng->problem().precision != DMRG_PREC_MIXED_BF16)
@@ -217,7 +224,7 @@ dmrg_status dmrg_sigma_ex(dmrg_handle* h, int32_t bond, const double* psi, doubl
 }
 
 dmrg_status dmrg_sigma_host(dmrg_handle* h, int32_t bond, const double* psi, double* sig) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !psi || !sig) return fail(DMRG_ERR_ARG, "null argument");
     dmrg_status s = ensure_bond(h, bond);
     if (s != DMRG_OK) return s;
@@ -235,7 +242,7 @@ dmrg_status dmrg_sigma_host(dmrg_handle* h, int32_t bond, const double* psi, dou
 
 dmrg_status dmrg_davidson(dmrg_handle* h, int32_t bond, double* psi, double tol, int32_t max_iter,
                           double* energy, int32_t* iterations) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !psi) return fail(DMRG_ERR_ARG, "null argument");
     if (!(tol > 0)) return fail(DMRG_ERR_ARG, "tol must be positive");
     dmrg_status s = ensure_bond(h, bond);
@@ -254,7 +261,7 @@ dmrg_status dmrg_davidson(dmrg_handle* h, int32_t bond, double* psi, double tol,
 
 dmrg_status dmrg_sweep_ex(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedule, double tol,
                           double* energies, int32_t flags, int32_t max_iter) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || n_sweeps <= 0) return fail(DMRG_ERR_ARG, "bad arguments");
     if (h->L < 3) return fail(DMRG_ERR_ARG, "sweeps need L >= 3");
     if (!(tol > 0)) return fail(DMRG_ERR_ARG, "tol must be positive");
@@ -293,7 +300,7 @@ dmrg_status dmrg_sweep(dmrg_handle* h, int32_t n_sweeps, const int32_t* D_schedu
 
 dmrg_status dmrg_sweep_log(dmrg_handle* h, int32_t* n_steps, const double** rows, int32_t* n_kept,
                            const int32_t** kept) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !n_steps || !rows || !n_kept || !kept) return fail(DMRG_ERR_ARG, "null argument");
     const auto& lg = h->eng->sweep_log_;
     h->log_rows.clear();
@@ -315,7 +322,7 @@ dmrg_status dmrg_sweep_log(dmrg_handle* h, int32_t* n_steps, const double** rows
 }
 
 dmrg_status dmrg_sweep_phases(dmrg_handle* h, double* seconds5) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !seconds5) return fail(DMRG_ERR_ARG, "bad arguments");
     for (int k = 0; k < 5; ++k) seconds5[k] = h->eng->phase_s[k];
     return DMRG_OK;
@@ -324,7 +331,7 @@ dmrg_status dmrg_sweep_phases(dmrg_handle* h, double* seconds5) {
 
 dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi, const double* lam,
                                 double* g1, double* g2) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !psi || !lam || !g1 || !g2) return fail(DMRG_ERR_ARG, "null argument");
     dmrg_status s = ensure_bond(h, bond);
     if (s != DMRG_OK) return s;
@@ -362,7 +369,7 @@ dmrg_status dmrg_sigma_backward(dmrg_handle* h, int32_t bond, const double* psi,
 }
 
 dmrg_status dmrg_set_integrals(dmrg_handle* h, const double* t, const double* v) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !t || !v) return fail(DMRG_ERR_ARG, "null argument");
     const int L = h->L;
     const size_t L2 = size_t(L) * L, L4 = L2 * L2;
@@ -377,7 +384,7 @@ dmrg_status dmrg_set_integrals(dmrg_handle* h, const double* t, const double* v)
 }
 
 dmrg_status dmrg_sweep_state(dmrg_handle* h, int32_t* bond, int64_t* psi_size, double* psi_dev) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !bond || !psi_size) return fail(DMRG_ERR_ARG, "null argument");
     const double* p = h->eng->sweep_psi();
     if (!p || h->eng->bond() < 0) return fail(DMRG_ERR_ARG, "no swept state (call dmrg_sweep first)");
@@ -392,7 +399,7 @@ dmrg_status dmrg_sweep_state(dmrg_handle* h, int32_t* bond, int64_t* psi_size, d
 }
 
 dmrg_status dmrg_set_state(dmrg_handle* h, int32_t bond, const double* psi) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !psi) return fail(DMRG_ERR_ARG, "null argument");
     if (h->eng->bond() != bond) return fail(DMRG_ERR_ARG, "bond not prepared (call dmrg_prepare)");
     h->eng->set_state(psi);
@@ -401,7 +408,7 @@ dmrg_status dmrg_set_state(dmrg_handle* h, int32_t bond, const double* psi) {
 }
 
 dmrg_status dmrg_expectation(dmrg_handle* h, int32_t bond, const double* lam, const double* psi, double* value) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !lam || !psi || !value) return fail(DMRG_ERR_ARG, "null argument");
     dmrg_status s = ensure_bond(h, bond);
     if (s != DMRG_OK) return s;
@@ -420,7 +427,7 @@ dmrg_status dmrg_expectation(dmrg_handle* h, int32_t bond, const double* lam, co
 }
 
 dmrg_status dmrg_orbital_gradient(dmrg_handle* h, const double* g1, const double* g2, double* grad) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !g1 || !g2 || !grad) return fail(DMRG_ERR_ARG, "null argument");
     dmrg::Exec* ex = h->ex.get();
     const int L = h->L;
@@ -436,7 +443,7 @@ dmrg_status dmrg_orbital_gradient(dmrg_handle* h, const double* g1, const double
 }
 
 dmrg_status dmrg_eigh_batch(dmrg_handle* h, int32_t nmat, const int32_t* n, double* A, double* w, double* Z) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !n || !A || !w || !Z) return fail(DMRG_ERR_ARG, "null argument");
     if (nmat <= 0) return fail(DMRG_ERR_ARG, "nmat must be positive");
     if (A == Z) return fail(DMRG_ERR_ARG, "A and Z must be different buffers");
@@ -459,7 +466,7 @@ dmrg_status dmrg_eigh_batch(dmrg_handle* h, int32_t nmat, const int32_t* n, doub
 }
 
 dmrg_status dmrg_two_site_rotate(dmrg_handle* h, int32_t bond, double theta, const double* psi, double* out) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !psi || !out) return fail(DMRG_ERR_ARG, "null argument");
     if (psi == out) return fail(DMRG_ERR_ARG, "psi and out must be different buffers");
     if (!std::isfinite(theta)) return fail(DMRG_ERR_ARG, "theta must be finite");
@@ -472,7 +479,7 @@ dmrg_status dmrg_two_site_rotate(dmrg_handle* h, int32_t bond, double theta, con
 }
 
 dmrg_status dmrg_half_renyi(dmrg_handle* h, int32_t bond, const double* psi, double* s_half) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !psi || !s_half) return fail(DMRG_ERR_ARG, "null argument");
     dmrg_status s = ensure_bond(h, bond);
     if (s != DMRG_OK) return s;
@@ -482,7 +489,7 @@ dmrg_status dmrg_half_renyi(dmrg_handle* h, int32_t bond, const double* psi, dou
 }
 
 dmrg_status dmrg_mode_step(dmrg_handle* h, double* theta, double* s_before, double* s_after) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !theta) return fail(DMRG_ERR_ARG, "null argument");
     if (!h->eng->sweep_psi() || h->eng->bond() < 0) return fail(DMRG_ERR_ARG, "no swept state (call dmrg_sweep first)");
     *theta = h->eng->mode_step(s_before, s_after);
@@ -492,7 +499,7 @@ dmrg_status dmrg_mode_step(dmrg_handle* h, double* theta, double* s_before, doub
 }
 
 dmrg_status dmrg_get_integrals(dmrg_handle* h, double* t, double* v) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !t || !v) return fail(DMRG_ERR_ARG, "null argument");
     std::copy(h->t_user.begin(), h->t_user.end(), t);
     std::copy(h->v_user.begin(), h->v_user.end(), v);
@@ -501,7 +508,7 @@ dmrg_status dmrg_get_integrals(dmrg_handle* h, double* t, double* v) {
 }
 
 dmrg_status dmrg_mode_log(dmrg_handle* h, int32_t* n, const double** rows) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !n || !rows) return fail(DMRG_ERR_ARG, "null argument");
     h->log_rows.clear();
     for (const auto& m : h->eng->mode_log_)
@@ -513,7 +520,7 @@ dmrg_status dmrg_mode_log(dmrg_handle* h, int32_t* n, const double** rows) {
 }
 
 dmrg_status dmrg_term_work(dmrg_handle* h, int32_t bond, int32_t* n_terms, int64_t* work) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !n_terms) return fail(DMRG_ERR_ARG, "null argument");
     dmrg_status s = ensure_bond(h, bond);
     if (s != DMRG_OK) return s;
@@ -548,7 +555,7 @@ dmrg_status dmrg_term_partition(int32_t n, const int64_t* work, int32_t world, i
 
 dmrg_status dmrg_sigma_subset(dmrg_handle* h, int32_t bond, const double* psi, double* sig, const int32_t* owner,
                               int32_t rank) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !psi || !sig || !owner) return fail(DMRG_ERR_ARG, "null argument");
     dmrg_status s = ensure_bond(h, bond);
     if (s != DMRG_OK) return s;
@@ -562,7 +569,7 @@ dmrg_status dmrg_sigma_subset(dmrg_handle* h, int32_t bond, const double* psi, d
 }
 
 dmrg_status dmrg_stats(dmrg_handle* h, int64_t* o) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !o) return fail(DMRG_ERR_ARG, "null argument");
     const dmrg::BondStats& s = h->eng->stats();
     o[0] = s.psi_size;
@@ -586,7 +593,7 @@ dmrg_status dmrg_stats(dmrg_handle* h, int64_t* o) {
 }
 
 dmrg_status dmrg_plan_paths(dmrg_handle* h, int64_t* o) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !o) return fail(DMRG_ERR_ARG, "null argument");
     if (h->eng->bond() < 0) return fail(DMRG_ERR_ARG, "no bond prepared");
     const dmrg::BondStats& s = h->eng->stats();
@@ -603,7 +610,7 @@ dmrg_status dmrg_plan_paths(dmrg_handle* h, int64_t* o) {
 }
 
 dmrg_status dmrg_graph_replays(dmrg_handle* h, int64_t* replays) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h || !replays) return fail(DMRG_ERR_ARG, "null argument");
     *replays = h->eng->graph_runs();
     return DMRG_OK;
@@ -611,7 +618,7 @@ dmrg_status dmrg_graph_replays(dmrg_handle* h, int64_t* replays) {
 }
 
 dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out) {
-  return guard([&]() -> dmrg_status {
+  return guard_h(h, [&]() -> dmrg_status {
     if (!h) return fail(DMRG_ERR_ARG, "null handle");
     if (mode != 0 && mode != 1) return fail(DMRG_ERR_ARG, "mode must be 0 or 1");
     h->eng->exec()->profile(mode, out);
@@ -622,6 +629,7 @@ dmrg_status dmrg_profile(dmrg_handle* h, int32_t mode, double* out) {
 void dmrg_destroy(dmrg_handle* h) {
   try {
     if (h) {
+      DmrgDeviceGuard dg(h->device);   // the handle's memory lives on its device
       dmrg_internal_handle_gone(h);
       h->eng.reset();
       h->ex.reset();

@@ -1,5 +1,7 @@
 // Handle layout and the status mapping shared by the C ABI translation units.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <memory>
 #include <new>
 #include <stdexcept>
@@ -61,6 +63,33 @@ dmrg_status dmrg_internal_guard(F&& f) {
   } catch (...) {
     return dmrg_internal_fail(DMRG_ERR_STATE, "unknown error");
   }
+}
+
+// Makes `device` the calling thread's current CUDA device for the guard's lifetime
+// and restores the previous one afterwards (device < 0: no change), so that an
+// entry point launches on its handle's device whatever device the caller has
+// made current since the handle was created.
+struct DmrgDeviceGuard {
+  int prev = -1;
+  explicit DmrgDeviceGuard(int device) {
+    int cur = -1;
+    if (device >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != device && cudaSetDevice(device) == cudaSuccess)
+      prev = cur;
+  }
+  ~DmrgDeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DmrgDeviceGuard(const DmrgDeviceGuard&) = delete;
+  DmrgDeviceGuard& operator=(const DmrgDeviceGuard&) = delete;
+};
+
+// dmrg_internal_guard with the handle's device current during the call
+template <class F>
+dmrg_status dmrg_internal_guard_on(int device, F&& f) {
+  return dmrg_internal_guard([&]() -> dmrg_status {
+    DmrgDeviceGuard dg(device);
+    return f();
+  });
 }
 
 // Reads the executor's device error word (a stream synchronisation): 9 = the

@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "mixed.h"
@@ -707,10 +708,16 @@ __global__ void df_to_f64_kernel(const float* __restrict__ hi, const float* __re
 void launch_mixed_gemm(const MixTile* tiles, int ntiles, const MixProb* probs, const MixSeg* segs,
                        const int64_t* bcol, const int64_t* ccol, const float* acol, int* err, int* next_tile,
                        int tn, int nsm, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(mixed_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    attr = true;
+  // the shared-memory opt-in is a per-device attribute of the kernel: set it once
+  // on every device that launches it (devices past 63 set it on every launch)
+  static std::atomic<uint64_t> attr_set{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t(1) << dev) : 0;
+  if (!bit || !(attr_set.load(std::memory_order_relaxed) & bit)) {
+    if (cudaFuncSetAttribute(mixed_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) ==
+        cudaSuccess)
+      attr_set.fetch_or(bit, std::memory_order_relaxed);
   }
   const int grid = ntiles < nsm ? ntiles : nsm;
   if (ntiles > 0) {
