@@ -117,6 +117,7 @@ class Dmrg:
         self.t = np.ascontiguousarray(t, dtype=np.float64)
         self.v = np.ascontiguousarray(v, dtype=np.float64)
         self.L = int(self.t.shape[0])
+        self._check_integrals(self.t, self.v)
         self.na, self.nb = int(na), int(nb)
         self._order = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
         p = _Problem(self.L, self.na, self.nb, _dp(self.t), _dp(self.v),
@@ -129,6 +130,12 @@ class Dmrg:
     def _check(self, st):
         if st != OK:
             raise DmrgError(st, self.lib.dmrg_last_error().decode())
+
+    def _check_integrals(self, t, v):
+        # the library reads L*L and L^4 doubles through these host pointers
+        L = self.L
+        if t.shape != (L, L) or v.shape != (L, L, L, L):
+            raise ValueError(f"integrals of shapes {t.shape}, {v.shape}; expected ({L}, {L}) and ({L},)*4")
 
     def close(self):
         if getattr(self, "h", None):
@@ -172,15 +179,24 @@ class Dmrg:
         self._check(self.lib.dmrg_sigma_ex(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.c_void_p(int(sig_ptr)),
                                            int(precision)))
 
+    def _host_psi(self, bond, psi):
+        """psi as a contiguous float64 host array of the prepared bond's psi_size (the library
+        reads and writes exactly that many doubles through host pointers)."""
+        psi = np.ascontiguousarray(psi, dtype=np.float64).ravel()
+        n = self.layout(bond)[1]
+        if psi.size != n:
+            raise ValueError(f"psi has {psi.size} elements; the wave function at bond {bond} has {n}")
+        return psi
+
     def sigma_host(self, bond, psi):
-        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        psi = self._host_psi(bond, psi)
         out = np.empty_like(psi)
         self._check(self.lib.dmrg_sigma_host(self.h, bond, _dp(psi), _dp(out)))
         return out
 
     def sigma_host_noalloc(self, bond, psi):
         """sigma with host buffers staged through the library's built-in device array (no allocation)."""
-        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        psi = self._host_psi(bond, psi)
         out = np.empty_like(psi)
         self._check(self.lib.dmrg_sigma_host_noalloc(self.h, bond, _dp(psi), _dp(out)))
         return out
@@ -244,8 +260,10 @@ class Dmrg:
 
     def set_integrals(self, t, v):
         """New integrals (caller's numbering) for the same MPS basis; block operators are rebuilt on demand."""
-        self.t = np.ascontiguousarray(t, dtype=np.float64)
-        self.v = np.ascontiguousarray(v, dtype=np.float64)
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        self._check_integrals(t, v)
+        self.t, self.v = t, v
         self._check(self.lib.dmrg_set_integrals(self.h, _dp(self.t), _dp(self.v)))
 
     def sweep_state(self, psi_ptr=None):
@@ -277,7 +295,10 @@ class Dmrg:
         return w
 
     def sigma_subset(self, bond, psi_ptr, sig_ptr, owner, rank):
-        own = np.ascontiguousarray(owner, dtype=np.int32)
+        own = np.ascontiguousarray(owner, dtype=np.int32).ravel()
+        n = len(self.term_work(bond))
+        if own.size != n:
+            raise ValueError(f"owner has {own.size} entries; the bond has {n} terms")
         self._check(self.lib.dmrg_sigma_subset(self.h, bond, ctypes.c_void_p(int(psi_ptr)), ctypes.c_void_p(int(sig_ptr)),
                                                own.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(rank)))
 
