@@ -124,3 +124,14 @@ def test_problem_validation_without_a_device(lib):
     st, msg = status(order=[0, 1, 1, 3])
     assert st == binding.ERR_ARG and "permutation" in msg
     assert status(order=[0, 1, 2, 4])[0] == binding.ERR_ARG
+
+
+def test_binding_rejects_integrals_of_the_wrong_shape(lib):
+    """The library reads L*L and L^4 doubles through the integral pointers: the binding
+    checks the shapes first, so a short array never reaches it (no device needed)."""
+    import numpy as np
+    from paper_2501_18263_gb300 import binding
+    with pytest.raises(ValueError):
+        binding.Dmrg(np.eye(4), np.zeros((3, 3, 3, 3)), 2, 2, lib=lib)
+    with pytest.raises(ValueError):
+        binding.Dmrg(np.zeros((4, 3)), np.zeros((4, 4, 4, 4)), 2, 2, lib=lib)
